@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Benchmark: point evaluations per second of the GPU point count.
+
+Workload (one "step"): g=2, q=31 and q=27, the full monic degree-5 and
+degree-6 families with zero x^(d-1) coefficient (q^4 + q^5 members each),
+counts over F_q and F_{q^2}, exact histograms -- all four jobs in one
+persistent launch replayed from a CUDA graph (clear, count, compact).
+
+value  = point evaluations of square-free members per second, device-timed
+         (CUDA events on the launch stream, L2 flushed between steps);
+e2e    = the same through the public C ABI with host results (descriptor
+         upload from pinned memory, launch, histogram copy-back and sort);
+plain  = the same jobs with one launch per job (no persistent queue, no graph).
+
+--impl reference times the CPU oracle (oracle/) on bounded samples of the
+same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1805_11991_gb300.workloads import CONFIGS, JobSpec  # noqa: E402
+
+METRIC = "point evals/s (square-free members x sum_k q^k), batched persistent launch"
+UNIT = "evals/s"
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hwc", choices=["hwc", "reference"])
+    ap.add_argument("--config", default="config2", choices=sorted(CONFIGS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def evals_per_member(spec: JobSpec) -> int:
+    return spec.nominal_evals_per_member()
+
+
+def lookups_per_eval(spec: JobSpec) -> float:
+    """Zech lookups per point evaluation of the Horner chain: one per nonzero
+    coefficient among c_0..c_{d-2} (c_{d-1} = 0, lead 1), i.e. (d-1)(q-1)/q on
+    average over the family."""
+    return (spec.degree - 1) * (spec.q - 1) / spec.q
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg and --impl reference)
+
+def oracle_rate(jobs, seconds: float, offset_frac: float = 0.0):
+    """Time the oracle on a bounded sample: the same number of members from
+    each job, starting at offset_frac of the family; returns
+    (evals/s of square-free members, members/s, threads, sample text)."""
+    import oracle
+    threads = os.cpu_count() or 1
+    # calibrate on a tiny slice
+    probe = 64 * threads
+    t0 = time.perf_counter()
+    for s in jobs:
+        oracle.count_polys(s.g, s.q, s.kind, s.degree, s.first, min(probe, s.n()),
+                           seed=s.seed, sample_count=s.sample_count, threads=threads)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    per = max(64, int(probe * seconds / dt))
+    evals = members = 0
+    t0 = time.perf_counter()
+    for s in jobs:
+        n = min(per, s.n())
+        first = s.first + int((s.n() - n) * offset_frac)
+        _, sqf = oracle.count_polys(s.g, s.q, s.kind, s.degree, first, n, seed=s.seed,
+                                    sample_count=s.sample_count, threads=threads)
+        evals += int(sqf.sum()) * evals_per_member(s)
+        members += n
+    dt = time.perf_counter() - t0
+    sample = f"{per} consecutive members of each of the {len(jobs)} jobs"
+    return evals / dt, members / dt, threads, sample
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    jobs = CONFIGS[args.config]()
+    per_step = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    for i in range(args.warmup):
+        oracle_rate(jobs, per_step / 4, offset_frac=(i + 0.5) / (args.warmup + 1))
+    rates = []
+    curves = []
+    threads = sample = None
+    for i in range(args.steps):
+        r, c, threads, sample = oracle_rate(jobs, per_step, offset_frac=i / max(1, args.steps))
+        rates.append(r)
+        curves.append(c)
+    value = statistics.mean(rates)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": per_step * 1000.0, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic (full families, exact decode)",
+        "config": {"workload": args.config, "jobs": [j.__dict__ for j in jobs]},
+        "curves_per_s": statistics.mean(curves),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"each step: {sample} (a different slice per step)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-i", str(self.gpu),
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.3)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[4:]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[3][1:]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows),
+                "reasons": sorted(reasons)}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("count_kernels.cu", "hwc_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1805_11991_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the count kernel from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    try:
+        with open(PROFILE_TRAFFIC) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    import torch
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    from paper_1805_11991_gb300 import hwc
+
+    jobs = CONFIGS[args.config]()        # every rank runs the whole workload (weak scaling)
+    hjobs = [hwc.make_job(s.g, s.q, s.kind, s.degree, s.first, s.n(), s.seed, s.sample_count) for s in jobs]
+    batched = hwc.Batch(hjobs, flags=hwc.FLAG_GRAPH | hwc.FLAG_TIMING)
+    plain = hwc.Batch(hjobs, flags=hwc.FLAG_PLAIN | hwc.FLAG_TIMING)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # warm-up (also fixes the square-free counts used as units)
+    for _ in range(max(args.warmup, 3)):
+        batched.launch(stream)
+        plain.launch(stream)
+    torch.cuda.synchronize()
+    results = [batched.result(i) for i in range(len(jobs))]
+    sqf = [h.n_squarefree for h in results]
+    units = sum(n * evals_per_member(s) for n, s in zip(sqf, jobs))
+    members = sum(s.n() for s in jobs)
+    lookups = sum(n * evals_per_member(s) * lookups_per_eval(s) for n, s in zip(sqf, jobs))
+
+    def timed(batch, k):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        kms = []
+        for a, b in ev:
+            with torch.cuda.stream(stream):
+                flush.zero_()                    # L2 flush, outside the timed events
+            a.record(stream)
+            batch.launch(stream)
+            b.record(stream)
+            kms.append(batch.kernel_ms())       # waits for this step
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev), kms
+
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        total_ms, kernel_ms = timed(batched, args.steps)
+    torch.cuda.synchronize()
+    barrier()
+    plain_ms, plain_kms = timed(plain, args.steps)
+
+    # e2e through the public API: launch + copy back + sort every job's histogram
+    e2e_steps = max(3, args.steps // 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        batched.launch(stream)
+        for i in range(len(jobs)):
+            batched.result(i)
+    e2e_s = time.perf_counter() - t0
+    h2d, d2h = batched.io_bytes()
+
+    if dist is not None:
+        t = torch.tensor([total_ms, plain_ms, e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, plain_ms, e2e_s = (float(v) for v in t.tolist())
+
+    # roofline of the dominant kernel (the persistent count kernel)
+    kern_ms = statistics.mean(kernel_ms)
+    achieved = lookups / (kern_ms * 1e-3) / 1e9
+    props = torch.cuda.get_device_properties(local_rank)
+    sms = props.multi_processor_count
+    sm_max = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            sm_max = json.load(fh).get("sm_max_mhz")
+    except (OSError, ValueError):
+        pass
+    sm_max = sm_max or 2070.0
+    peak = sms * sm_max * 1e6 * 32 / 1e9          # one 32-lane LDS wavefront per SM per clock
+    table_entries = 2 * (31 ** 2 - 1) + 1
+    measured = hwc.probe_smem_gather(table_entries, 4096) / 1e9
+    traffic = profiled_traffic()
+
+    value = world * units * args.steps / (total_ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic: full coefficient families decoded on the device",
+        "config": {"workload": args.config, "jobs": [f"g{s.g} q{s.q} d{s.degree} members {s.n()}" for s in jobs],
+                   "members": members, "squarefree": sum(sqf), "l2": "flushed (512 MiB write) between steps",
+                   "launch": "persistent kernel in a CUDA graph"},
+        "curves_per_s": world * members * args.steps / (total_ms * 1e-3),
+        "plain": {"value": world * units * args.steps / (plain_ms * 1e-3), "unit": UNIT,
+                  "ms_per_step": plain_ms / args.steps, "launches_per_step": plain.kernel_launches()},
+        "e2e": {"value": world * units * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps * batched.kernel_launches(),
+        "roofline": {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "Glookup/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "k_persistent",
+                     "kernel_ms": kern_ms,
+                     "peak_source": f"{sms} SMs x {sm_max:.0f} MHz x 32 lanes (bank-conflict-free LDS)",
+                     "measured_random_gather": measured,
+                     "frac_of_measured_random_gather": achieved / measured},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r, c, threads, sample = oracle_rate(jobs, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": sample, "curves_per_s": c}
+    line["clocks"] = clk.summary()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    batched.close()
+    plain.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

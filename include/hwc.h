@@ -1,0 +1,235 @@
+/*
+ * hwc.h -- C ABI of the GB300 point-counting library (libhwc.so).
+ *
+ * The library counts points on every hyperelliptic curve C_f : y^2 = f(x) of
+ * genus g in a coefficient family over F_q, over every F_{q^k}, k = 1..g, and
+ * returns the exact histogram of the tuples (#C_f(F_q), ..., #C_f(F_{q^g}))
+ * over the square-free members f.  This is the inner part of Algorithm 1 of
+ * Raum, "Hyperelliptic curves over small finite fields and GPU accelerators"
+ * (arXiv:1805.11991): lines 3-17 and the increment of line 21 with weight 1.
+ *
+ * Conventions shared by every entry point
+ *  - Return value: HWC_OK (0) or a negative HWC_ERR_* code.  Nothing throws
+ *    across the ABI.  hwc_last_error() gives a message for the calling thread.
+ *  - q is an odd prime power, 1 <= g <= 4, 1 <= k <= g, deg f = d in
+ *    {2g+1, 2g+2} (Sec. 1.1).  Q = q^k must be at most HWC_MAX_Q.
+ *  - F_q digits: an integer c in [0, q), c = sum_i b_i p^i, stands for
+ *    sum_i b_i T^i in F_p[T]/m(T), m the first monic irreducible polynomial of
+ *    degree e (q = p^e) in the order of the index sum_i m_i p^i.  So 0 and 1
+ *    are the field's 0 and 1.  Coefficient c_i of f is digit i of the member
+ *    index, base q, little endian (see hwc_family_t).
+ *  - Handles (hwc_tables_t, hwc_hist_t, hwc_batch_t, hwc_server_t) are owned
+ *    by the library and released with their *_free / *_close function.
+ *    Device memory behind them is allocated by the library on the current
+ *    CUDA device.
+ *  - `stream` arguments are a cudaStream_t passed as void* (NULL = the
+ *    default stream).
+ */
+#ifndef HWC_H
+#define HWC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HWC_OK 0
+#define HWC_ERR_ARG (-1)       /* bad q, g, k, degree, family or flags      */
+#define HWC_ERR_RANGE (-2)     /* first + count beyond the family           */
+#define HWC_ERR_TOO_LARGE (-3) /* Q above HWC_MAX_Q, or histogram overflow  */
+#define HWC_ERR_NOMEM (-4)     /* device or host allocation failed          */
+#define HWC_ERR_CUDA (-5)      /* a CUDA call failed (message has details)  */
+#define HWC_ERR_TIMEOUT (-6)   /* a bounded wait ran out                    */
+#define HWC_ERR_BUSY (-7)      /* server admission refused (no room)        */
+#define HWC_ERR_STATE (-8)     /* call out of order (e.g. result not ready) */
+
+#define HWC_MAX_Q 262144u      /* largest field size F_{q^k} accepted       */
+#define HWC_MAX_G 4u
+
+/* Families of f (Sec. 1.1, Algorithm 1 line 3).  Member idx decodes to
+ * c_0..c_d by base-q digits of idx, little endian:
+ *  HWC_FAM_ALL_DEG       exact degree d, any lead: c_i = digit i of
+ *                        (idx mod q^d) for i < d, c_d = 1 + floor(idx / q^d);
+ *                        (q-1) q^d members.
+ *  HWC_FAM_MONIC_NOSUB   monic, c_{d-1} = 0, (c_0..c_{d-2}) = digits of idx;
+ *                        q^(d-1) members.
+ *  HWC_FAM_MONIC_NOSUB_SAMPLED
+ *                        member j (0 <= j < sample_count) is member
+ *                        floor(z_j * q^(d-1) / 2^64) of HWC_FAM_MONIC_NOSUB,
+ *                        z_j the SplitMix64 output for state seed + (j+1) *
+ *                        0x9E3779B97F4A7C15 (Steele, Lea, Flood 2014);
+ *                        drawn with replacement. */
+#define HWC_FAM_ALL_DEG 0u
+#define HWC_FAM_MONIC_NOSUB 1u
+#define HWC_FAM_MONIC_NOSUB_SAMPLED 2u
+
+typedef struct {
+    uint32_t kind;          /* HWC_FAM_*                                   */
+    uint32_t degree;        /* d                                           */
+    uint64_t seed;          /* sampled family only                         */
+    uint64_t sample_count;  /* sampled family only                         */
+} hwc_family_t;
+
+/* One counting job: members [first, first + count) of a family. */
+typedef struct {
+    uint32_t g;
+    uint32_t q;
+    hwc_family_t family;
+    uint64_t first;
+    uint64_t count;
+} hwc_job_t;
+
+typedef struct hwc_tables hwc_tables_t;
+typedef struct hwc_hist hwc_hist_t;
+typedef struct hwc_batch hwc_batch_t;
+typedef struct hwc_server hwc_server_t;
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *hwc_last_error(void);
+
+/* Library version string. */
+const char *hwc_version(void);
+
+/* ------------------------------------------------------------------ */
+/* Field tables (Sec. 2.3, eq. 3.1-3.2)                                */
+
+/* Build, on the current device, the Zech-logarithm tables of F_Q, Q = q^k:
+ * a primitive element alpha (F_Q = F_p[X]/M(X), M the first primitive
+ * polynomial of degree e*k over F_p by index, alpha = X), antilog[i] =
+ * alpha^i, log (log of 0 = L = Q-1, the encoding of eq. 3.1), the Zech table
+ * Z[n] = log(1 + alpha^n) with Z[L/2] = L (eq. 3.2), and the logs of the F_q
+ * digits embedded in F_Q.  *out receives a library-owned handle; errors:
+ * HWC_ERR_ARG (q not an odd prime power, k = 0), HWC_ERR_TOO_LARGE
+ * (Q > HWC_MAX_Q), HWC_ERR_NOMEM, HWC_ERR_CUDA.  Synchronous. */
+int hwc_field_tables(uint32_t q, uint32_t k, hwc_tables_t **out);
+
+/* Facts about built tables.  info[0..] = q, k, p, e, Q, L, primitive-poly
+ * degree n = e*k, then M_0..M_n (n+1 values), then the digit modulus
+ * m_0..m_e (e+1 values).  `cap` is the length of info; returns the number
+ * of values written, or a negative error. */
+int hwc_tables_info(const hwc_tables_t *t, uint32_t *info, uint32_t cap);
+
+/* Copy the tables to host arrays (any may be NULL): antilog[L] (element of
+ * F_Q as the integer sum_i a_i p^i of its coefficients on 1, X, X^2, ...),
+ * log[Q], zech[L], coef_log[q].  Synchronous. */
+int hwc_tables_read(const hwc_tables_t *t, uint32_t *antilog, uint32_t *log,
+                    uint32_t *zech, uint32_t *coef_log);
+
+void hwc_tables_free(hwc_tables_t *t);
+
+/* ------------------------------------------------------------------ */
+/* Counting                                                            */
+
+/* Number of members of a family over F_q into *n. */
+int hwc_family_size(uint32_t q, const hwc_family_t *fam, uint64_t *n);
+
+/* Flags for hwc_count / hwc_batch_create. */
+#define HWC_FLAG_PLAIN 0x1u       /* one launch per job (no persistent queue)  */
+#define HWC_FLAG_GRAPH 0x2u       /* capture the launch sequence in a CUDA graph */
+#define HWC_FLAG_HORNER 0x4u      /* force the per-member Horner kernel        */
+#define HWC_FLAG_NO_TUNE 0x8u     /* skip the autotuner, use defaults          */
+#define HWC_FLAG_TIMING 0x10u     /* time the count kernel(s) with CUDA events */
+
+/* Histogram of (#C(F_q), ..., #C(F_{q^g})) over the square-free members
+ * [first, first+count) of the family (Algorithm 1 lines 3-17 and 21, every
+ * weight 1).  Synchronous on `stream`; *out receives a library-owned
+ * histogram.  Errors: HWC_ERR_ARG, HWC_ERR_RANGE, HWC_ERR_TOO_LARGE,
+ * HWC_ERR_NOMEM, HWC_ERR_CUDA. */
+int hwc_count(uint32_t g, uint32_t q, const hwc_family_t *fam, uint64_t first,
+              uint64_t count, uint32_t flags, void *stream, hwc_hist_t **out);
+
+/* Per-member counts (for checking): counts[i*g + k-1] = #C(F_{q^k}) and
+ * sqf[i] = 1 if member first+i is square-free.  With unfiltered = 0 the
+ * counts of non-square-free members are 0; with unfiltered = 1 they are the
+ * point-count formula applied anyway.  `counts` (count*g int32) and `sqf`
+ * (count bytes) are HOST arrays.  Synchronous. */
+int hwc_count_members(uint32_t g, uint32_t q, const hwc_family_t *fam,
+                      uint64_t first, uint64_t count, int unfiltered,
+                      void *stream, int32_t *counts, uint8_t *sqf);
+
+/* Histogram contents.  n_entries distinct tuples; n_squarefree = sum of the
+ * multiplicities; n_total = members examined. */
+int hwc_hist_size(const hwc_hist_t *h, uint64_t *n_entries, uint64_t *n_squarefree,
+                  uint64_t *n_total);
+/* g of the histogram. */
+int hwc_hist_genus(const hwc_hist_t *h, uint32_t *g);
+/* Host arrays: counts[n_entries*g] (#C_1..#C_g per entry, sorted
+ * lexicographically), mult[n_entries]. */
+int hwc_hist_read(const hwc_hist_t *h, int32_t *counts, uint64_t *mult);
+/* into += from (same g); shards of one family and resumed runs add up. */
+int hwc_hist_merge(hwc_hist_t *into, const hwc_hist_t *from);
+/* New histogram from host arrays (e.g. a checkpoint), same layout as read. */
+int hwc_hist_from_arrays(uint32_t g, uint64_t n_entries, const int32_t *counts,
+                         const uint64_t *mult, uint64_t n_total, hwc_hist_t **out);
+void hwc_hist_free(hwc_hist_t *h);
+
+/* ------------------------------------------------------------------ */
+/* Batched execution: many jobs in one persistent launch               */
+
+/* Prepare a batch: builds (or reuses) the field tables of every job,
+ * allocates one device histogram per job and the work queue, and picks the
+ * kernel parameters (autotuned unless HWC_FLAG_NO_TUNE).  With HWC_FLAG_PLAIN
+ * each job gets its own launch instead of one persistent launch.  With
+ * HWC_FLAG_GRAPH the launch sequence is captured once in a CUDA graph. */
+int hwc_batch_create(const hwc_job_t *jobs, size_t n_jobs, uint32_t flags,
+                     hwc_batch_t **out);
+/* Enqueue one complete run of the batch on `stream` (asynchronous): clears
+ * the histograms and the queue, then runs every job. */
+int hwc_batch_launch(hwc_batch_t *b, void *stream);
+/* Wait for the last launch, copy out and sort the histogram of job i. */
+int hwc_batch_result(hwc_batch_t *b, size_t i, hwc_hist_t **out);
+/* Number of kernel launches one hwc_batch_launch enqueues. */
+int hwc_batch_kernel_launches(const hwc_batch_t *b, uint32_t *n);
+/* Bytes one hwc_batch_launch copies host->device (job descriptors, from
+ * pinned memory) and hwc_batch_result copies device->host for all jobs of
+ * the last launch (statistics plus the compacted histograms). */
+int hwc_batch_io_bytes(const hwc_batch_t *b, uint64_t *h2d, uint64_t *d2h);
+/* With HWC_FLAG_TIMING: device time in ms of the count kernel(s) of the last
+ * launch (CUDA events on the launch stream), after waiting for it. */
+int hwc_batch_kernel_ms(hwc_batch_t *b, float *ms);
+void hwc_batch_free(hwc_batch_t *b);
+/* Convenience: create, launch, wait, results for every job (outs[n_jobs]). */
+int hwc_batch_run(const hwc_job_t *jobs, size_t n_jobs, uint32_t flags, void *stream,
+                  hwc_hist_t **outs);
+
+/* ------------------------------------------------------------------ */
+/* Serving: a request loop with continuous batching                    */
+
+typedef struct {
+    uint64_t device_bytes;   /* admission budget for tables + histograms    */
+    uint32_t max_active;     /* jobs on the device at once                  */
+    uint32_t step_items;     /* work per device step (0 = library default)  */
+} hwc_server_config_t;
+
+/* Start a server thread that keeps field tables resident and runs, step
+ * after step, one batched launch over the active requests; requests that
+ * arrive meanwhile join at the next step once memory and a slot are free. */
+int hwc_serve_open(const hwc_server_config_t *cfg, hwc_server_t **out);
+/* Queue a request; *ticket identifies it. */
+int hwc_serve_submit(hwc_server_t *s, const hwc_job_t *job, uint64_t *ticket);
+/* Non-blocking: HWC_OK with *out set when done, HWC_ERR_STATE if not yet.
+ * timeout_ms > 0 waits at most that long. */
+int hwc_serve_poll(hwc_server_t *s, uint64_t ticket, uint32_t timeout_ms,
+                   hwc_hist_t **out);
+/* Latency of a finished request: submit -> admitted -> done, microseconds. */
+int hwc_serve_latency(hwc_server_t *s, uint64_t ticket, double *queued_us,
+                      double *total_us);
+/* Stop the thread (finishing the active step) and free everything. */
+int hwc_serve_close(hwc_server_t *s);
+
+/* ------------------------------------------------------------------ */
+/* Measurement                                                         */
+
+/* Rate of dependent, uniformly random 16-bit reads from a shared-memory
+ * table of `entries` entries (32..100000), the access pattern Sec. 4 names
+ * as the limit of Zech arithmetic on GPUs; `iters` reads per chain, four
+ * chains per thread, all SMs.  The denominator of the lookup roofline.
+ * Synchronous, current device. */
+int hwc_probe_smem_gather(uint32_t entries, uint32_t iters, double *reads_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HWC_H */

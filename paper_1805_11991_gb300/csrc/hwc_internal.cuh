@@ -1,0 +1,138 @@
+// hwc_internal.cuh -- internal types of libhwc (not part of the C ABI).
+//
+// Element encoding (eq. 3.1): a nonzero element alpha^i of F_Q is stored as
+// its log i in [0, L), L = Q - 1; zero is stored as L.  L is even because q
+// is odd, so the quadratic character of alpha^i is (-1)^i (Sec. 1.1, chi).
+#pragma once
+
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+#include <mutex>
+#include <cuda_runtime.h>
+
+#include "../../include/hwc.h"
+
+namespace hwc {
+
+constexpr int kMaxG = 4;
+constexpr int kMaxD = 2 * kMaxG + 2;        // degree 2g+2
+constexpr int kMaxN = 12;                   // degree of F_Q over F_p (Q <= 2^18)
+constexpr int kMaxE = 8;                    // degree of F_q over F_p
+constexpr uint32_t kWideTable = 0xFFFFFFFFu; // table read from global memory
+constexpr unsigned long long kEmptyKey = ~0ull;
+constexpr int kTileMembers = 32;            // members per warp tile
+
+// ---------------------------------------------------------------------
+// errors (thread-local message, see hwc_last_error)
+int set_error(int code, const char *fmt, ...);
+#define HWC_CUDA_TRY(expr)                                                     \
+    do {                                                                       \
+        cudaError_t _e = (expr);                                               \
+        if (_e != cudaSuccess)                                                 \
+            return ::hwc::set_error(HWC_ERR_CUDA, "%s failed: %s (%s:%d)",     \
+                                    #expr, cudaGetErrorString(_e), __FILE__,   \
+                                    __LINE__);                                 \
+    } while (0)
+
+// ---------------------------------------------------------------------
+// field tables of F_Q, Q = q^k, resident on one device
+struct Tables {
+    uint32_t q = 0, k = 0, p = 0, e = 0, n = 0, Q = 0, L = 0;
+    uint32_t M[kMaxN + 1] = {};     // primitive modulus over F_p, M[n] = 1
+    uint32_t mq[kMaxE + 1] = {};    // digit-convention modulus of F_q
+    int device = -1;
+    uint32_t *d_antilog = nullptr;  // [L]
+    uint32_t *d_log = nullptr;      // [Q]
+    uint32_t *d_zech = nullptr;     // [L], Z[L/2] = L
+    uint32_t *d_coef_log = nullptr; // [q]
+    // Zech table in the layout the count kernels read: entry u in [0, 2L)
+    // is Z[u mod L], with the "1 + alpha^u = 0" entry replaced by the poison
+    // value 2L, and entry 2L = 2L (absorbing).  u16 when 2L < 65536.
+    uint16_t *d_zech2 = nullptr;    // [2L+1] or null
+    uint32_t *d_zech2w = nullptr;   // [2L+1]
+};
+
+int tables_build(uint32_t q, uint32_t k, Tables **out);
+void tables_destroy(Tables *t);
+// process-wide cache of tables per (device, q, k); never freed before exit
+int tables_cached(uint32_t q, uint32_t k, const Tables **out);
+
+// factor q = p^e, p odd prime
+bool prime_power(uint32_t q, uint32_t *p, uint32_t *e);
+
+// ---------------------------------------------------------------------
+// device job descriptor (plain struct copied to device memory)
+struct KJob {
+    uint32_t g, q, d, kind;
+    uint32_t p, unfiltered, pad0, pad1;
+    uint64_t seed, first, count;
+    uint64_t fam_mz;                  // q^(d-1): size of the MONIC_NOSUB family
+    uint64_t qd;                      // q^d (ALL_DEG decode)
+    uint64_t n_tiles;                 // ceil(count / 32)
+    uint32_t Q[kMaxG], L[kMaxG];
+    uint32_t barrett[kMaxG];          // floor(2^32 / L)
+    uint32_t tab_off[kMaxG];          // u16 offset of zech2 in smem or kWideTable
+    uint32_t coef_off[kMaxG];         // u32 offset of coef_log in smem (after tables)
+    const uint16_t *zech2[kMaxG];
+    const uint32_t *zech2w[kMaxG];
+    const uint32_t *coef_log[kMaxG];
+    uint32_t smem_u16;                // u16 words of zech2 tables staged in smem
+    uint32_t smem_bytes;              // total dynamic smem for this job
+    // outputs
+    unsigned long long *hkeys;        // [hmask+1]
+    unsigned long long *hcounts;      // [hmask+1]
+    uint32_t hmask, pad2;
+    unsigned long long *stats;        // [0] examined, [1] square-free, [2] overflow
+    int32_t *member_counts;           // per-member mode: [count*g]
+    uint8_t *member_sqf;              // per-member mode: [count]
+    unsigned long long *out_keys;     // compacted histogram [hmask+1]
+    unsigned long long *out_counts;
+    unsigned long long *n_out;        // number of compacted entries
+};
+
+// launch helpers (count_kernels.cu)
+struct LaunchShape {
+    int block = 256;       // threads per CTA (multiple of 32)
+    int grid = 0;          // CTAs (0 = derive)
+    int item_tiles = 4;    // tiles per queue item (persistent)
+};
+int launch_clear(const KJob *d_jobs, uint32_t n_jobs, unsigned long long *d_counter, cudaStream_t s);
+int launch_plain(const KJob *d_job, const KJob &h_job, const LaunchShape &sh, cudaStream_t s);
+int launch_persistent(const KJob *d_jobs, const uint64_t *d_item_start, uint32_t n_jobs,
+                      uint64_t n_items, unsigned long long *d_counter, uint32_t max_smem,
+                      const LaunchShape &sh, cudaStream_t s);
+int launch_compact(const KJob *d_jobs, uint32_t n_jobs, cudaStream_t s);
+// raise the dynamic shared memory limit of the count kernels (once per device)
+int prepare_count_kernels(void);
+int max_ctas_per_sm(int block, uint32_t smem_bytes, bool persistent, int *out);
+int device_sm_count(void);
+uint32_t device_smem_optin(void);
+
+// fills the job's smem layout (tab_off, coef_off, smem_bytes) given tables
+void layout_job_smem(KJob &j, uint32_t smem_limit);
+// validates a job and fills a KJob (tables, layout); outputs left null
+int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n);
+// hash slots for a job of `count` members (power of two)
+uint32_t hash_capacity(uint32_t g, uint32_t q, uint64_t count, uint32_t scale);
+
+}  // namespace hwc
+
+// opaque ABI types
+struct hwc_tables {
+    hwc::Tables *t;
+};
+
+struct hwc_hist {
+    uint32_t g = 0;
+    std::vector<int32_t> counts;   // n * g, lexicographically sorted
+    std::vector<uint64_t> mult;
+    uint64_t n_total = 0, n_sqf = 0;
+};
+
+namespace hwc {
+// decode compacted (key, count) pairs into a sorted histogram
+hwc_hist *hist_from_keys(const KJob &kj, const unsigned long long *keys,
+                         const unsigned long long *cnt, uint64_t n, uint64_t n_total);
+}  // namespace hwc

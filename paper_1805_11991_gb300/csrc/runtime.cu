@@ -1,0 +1,690 @@
+// runtime.cu -- host side of libhwc: jobs, batches (plain / persistent / CUDA
+// graph), histograms and the per-member checking path.
+#include "hwc_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <numeric>
+
+namespace hwc {
+
+static thread_local std::string g_err;
+
+int set_error(int code, const char *fmt, ...)
+{
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+// ---------------------------------------------------------------------
+// job validation
+
+static bool mul_ok(uint64_t a, uint64_t b, uint64_t *out)
+{
+    if (a && b > ~0ull / a) return false;
+    *out = a * b;
+    return true;
+}
+
+static bool upow(uint64_t b, uint32_t e, uint64_t *out)
+{
+    uint64_t r = 1;
+    for (uint32_t i = 0; i < e; ++i)
+        if (!mul_ok(r, b, &r)) return false;
+    *out = r;
+    return true;
+}
+
+static int family_size(uint32_t q, const hwc_family_t *fam, uint64_t *n)
+{
+    uint32_t p, e;
+    if (!fam) return set_error(HWC_ERR_ARG, "family is NULL");
+    if (!prime_power(q, &p, &e)) return set_error(HWC_ERR_ARG, "q=%u is not an odd prime power", q);
+    const uint32_t d = fam->degree;
+    if (d < 3 || d > (uint32_t)kMaxD) return set_error(HWC_ERR_ARG, "degree %u outside [3,%d]", d, kMaxD);
+    uint64_t v;
+    switch (fam->kind) {
+    case HWC_FAM_ALL_DEG:
+        if (!upow(q, d, &v) || !mul_ok(v, q - 1, &v)) return set_error(HWC_ERR_TOO_LARGE, "family size overflows");
+        break;
+    case HWC_FAM_MONIC_NOSUB:
+        if (!upow(q, d - 1, &v)) return set_error(HWC_ERR_TOO_LARGE, "family size overflows");
+        break;
+    case HWC_FAM_MONIC_NOSUB_SAMPLED:
+        if (!upow(q, d - 1, &v)) return set_error(HWC_ERR_TOO_LARGE, "family size overflows");
+        v = fam->sample_count;
+        break;
+    default:
+        return set_error(HWC_ERR_ARG, "unknown family kind %u", fam->kind);
+    }
+    *n = v;
+    return HWC_OK;
+}
+
+static int validate_job(const hwc_job_t &j, uint64_t *fam_n)
+{
+    if (j.g < 1 || j.g > (uint32_t)kMaxG) return set_error(HWC_ERR_ARG, "g=%u outside [1,%d]", j.g, kMaxG);
+    const uint32_t d = j.family.degree;
+    if (d != 2 * j.g + 1 && d != 2 * j.g + 2)
+        return set_error(HWC_ERR_ARG, "degree %u is not 2g+1 or 2g+2 for g=%u", d, j.g);
+    int rc = family_size(j.q, &j.family, fam_n);
+    if (rc) return rc;
+    uint64_t Qg;
+    if (!upow(j.q, j.g, &Qg) || Qg > HWC_MAX_Q)
+        return set_error(HWC_ERR_TOO_LARGE, "q^g above %u", HWC_MAX_Q);
+    if (j.first > *fam_n || j.count > *fam_n - j.first)
+        return set_error(HWC_ERR_RANGE, "members [%llu, +%llu) outside the family of %llu",
+                         (unsigned long long)j.first, (unsigned long long)j.count,
+                         (unsigned long long)*fam_n);
+    return HWC_OK;
+}
+
+// ---------------------------------------------------------------------
+// shared-memory layout of one job: u16 Zech tables first, then u32 coef logs
+
+void layout_job_smem(KJob &j, uint32_t smem_limit)
+{
+    // try to place every k; drop the largest tables to global until it fits
+    bool in_smem[kMaxG] = {};
+    for (uint32_t k = 0; k < j.g; ++k) in_smem[k] = j.zech2[k] != nullptr;
+    auto bytes_for = [&](void) {
+        uint64_t u16 = 0;
+        for (uint32_t k = 0; k < j.g; ++k)
+            if (in_smem[k]) u16 += ((2ull * j.L[k] + 1 + 7) / 8) * 8;
+        return u16 * 2 + 4ull * j.g * ((j.q + 3) / 4) * 4;
+    };
+    while (bytes_for() > smem_limit) {
+        int big = -1;
+        for (uint32_t k = 0; k < j.g; ++k)
+            if (in_smem[k] && (big < 0 || j.L[k] > j.L[big])) big = (int)k;
+        if (big < 0) break;
+        in_smem[big] = false;
+    }
+    uint32_t off = 0;
+    for (uint32_t k = 0; k < kMaxG; ++k) {
+        if (k < j.g && in_smem[k]) {
+            j.tab_off[k] = off;
+            off += ((2 * j.L[k] + 1 + 7) / 8) * 8;
+        } else {
+            j.tab_off[k] = kWideTable;
+        }
+    }
+    j.smem_u16 = off;
+    uint32_t off32 = off / 2;
+    for (uint32_t k = 0; k < kMaxG; ++k) {
+        j.coef_off[k] = off32;
+        if (k < j.g) off32 += ((j.q + 3) / 4) * 4;
+    }
+    j.smem_bytes = off32 * 4;
+}
+
+static uint32_t next_pow2(uint64_t v)
+{
+    uint64_t c = 1;
+    while (c < v) c <<= 1;
+    return (uint32_t)std::min<uint64_t>(c, 1ull << 31);
+}
+
+// number of (a_1..a_g) tuples allowed by the Hasse-Weil bound |a_k| <= 2g sqrt(q^k)
+static uint64_t hasse_weil_box(uint32_t g, uint32_t q)
+{
+    double box = 1;
+    double Q = 1;
+    for (uint32_t k = 1; k <= g; ++k) {
+        Q *= q;
+        double b = std::floor(2.0 * g * std::sqrt(Q));
+        box *= 2 * b + 1;
+    }
+    return box > 1e18 ? (uint64_t)1e18 : (uint64_t)box;
+}
+
+struct HostJob {
+    hwc_job_t job;
+    KJob kj;
+    uint64_t fam_n;
+};
+
+int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n)
+{
+    int rc = validate_job(jb, fam_n);
+    if (rc) return rc;
+    std::memset(&kj, 0, sizeof kj);
+    uint32_t p, e;
+    prime_power(jb.q, &p, &e);
+    kj.g = jb.g;
+    kj.q = jb.q;
+    kj.d = jb.family.degree;
+    kj.kind = jb.family.kind;
+    kj.p = p;
+    kj.seed = jb.family.seed;
+    kj.first = jb.first;
+    kj.count = jb.count;
+    upow(jb.q, kj.d - 1, &kj.fam_mz);
+    kj.qd = kj.fam_mz * jb.q;
+    kj.n_tiles = (jb.count + kTileMembers - 1) / kTileMembers;
+    for (uint32_t k = 1; k <= jb.g; ++k) {
+        const Tables *t = nullptr;
+        rc = tables_cached(jb.q, k, &t);
+        if (rc) return rc;
+        kj.Q[k - 1] = t->Q;
+        kj.L[k - 1] = t->L;
+        kj.barrett[k - 1] = (uint32_t)((1ull << 32) / t->L);
+        kj.zech2[k - 1] = t->d_zech2;
+        kj.zech2w[k - 1] = t->d_zech2w;
+        kj.coef_log[k - 1] = t->d_coef_log;
+    }
+    layout_job_smem(kj, std::min<uint32_t>(device_smem_optin(), 200u * 1024u));
+    return HWC_OK;
+}
+
+uint32_t hash_capacity(uint32_t g, uint32_t q, uint64_t count, uint32_t scale)
+{
+    uint64_t bound = std::min<uint64_t>(count, hasse_weil_box(g, q));
+    uint32_t cap = next_pow2(std::max<uint64_t>(256, 2 * bound * scale));
+    return std::min<uint32_t>(cap, 1u << 28);
+}
+
+}  // namespace hwc
+
+using namespace hwc;
+
+// ---------------------------------------------------------------------
+// histograms
+
+static hwc_hist *hist_from_map(uint32_t g, const std::map<std::vector<int32_t>, uint64_t> &m,
+                               uint64_t n_total)
+{
+    hwc_hist *h = new hwc_hist();
+    h->g = g;
+    h->n_total = n_total;
+    h->counts.reserve(m.size() * g);
+    h->mult.reserve(m.size());
+    for (auto &kv : m) {
+        h->counts.insert(h->counts.end(), kv.first.begin(), kv.first.end());
+        h->mult.push_back(kv.second);
+        h->n_sqf += kv.second;
+    }
+    return h;
+}
+
+hwc_hist *hwc::hist_from_keys(const KJob &kj, const unsigned long long *keys,
+                              const unsigned long long *cnt, uint64_t n, uint64_t n_total)
+{
+    const uint32_t g = kj.g;
+    std::vector<uint64_t> order(n);
+    std::vector<int32_t> tup(n * g);
+    for (uint64_t i = 0; i < n; ++i) {
+        for (uint32_t k = 0; k < g; ++k) {
+            int a = (int)((keys[i] >> (16 * k)) & 0xFFFFu) - 32768;
+            tup[i * g + k] = (int32_t)kj.Q[k] + 1 - a;   // #C = Q + 1 - a (eq. 1.1)
+        }
+    }
+    std::iota(order.begin(), order.end(), 0);
+    std::sort(order.begin(), order.end(), [&](uint64_t x, uint64_t y) {
+        return std::lexicographical_compare(&tup[x * g], &tup[x * g] + g, &tup[y * g], &tup[y * g] + g);
+    });
+    hwc_hist *h = new hwc_hist();
+    h->g = g;
+    h->n_total = n_total;
+    h->counts.resize(n * g);
+    h->mult.resize(n);
+    for (uint64_t i = 0; i < n; ++i) {
+        std::copy(&tup[order[i] * g], &tup[order[i] * g] + g, &h->counts[i * g]);
+        h->mult[i] = cnt[order[i]];
+        h->n_sqf += cnt[order[i]];
+    }
+    return h;
+}
+
+// ---------------------------------------------------------------------
+// batches
+
+struct hwc_batch {
+    std::vector<HostJob> jobs;
+    KJob *h_jobs = nullptr;          // pinned copy of the descriptors
+    uint64_t *h_item_start = nullptr;
+    KJob *d_jobs = nullptr;
+    uint64_t *d_item_start = nullptr;
+    uint64_t n_items = 0;
+    unsigned long long *d_counter = nullptr;
+    std::vector<void *> allocs;
+    uint32_t flags = 0;
+    LaunchShape shape;
+    uint32_t max_smem = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaEvent_t done = nullptr;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;   // HWC_FLAG_TIMING
+    bool launched = false;
+    uint64_t d2h_last = 0;
+    int device = 0;
+    uint32_t launches_per_run = 0;
+};
+
+static void batch_release(hwc_batch *b)
+{
+    if (!b) return;
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->t0) cudaEventDestroy(b->t0);
+    if (b->t1) cudaEventDestroy(b->t1);
+    if (b->h_jobs) cudaFreeHost(b->h_jobs);
+    if (b->h_item_start) cudaFreeHost(b->h_item_start);
+    for (void *p : b->allocs) cudaFree(p);
+    delete b;
+}
+
+template <class T>
+static int dalloc(hwc_batch *b, T **p, uint64_t n)
+{
+    void *v = nullptr;
+    if (cudaMalloc(&v, std::max<uint64_t>(n, 1) * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(HWC_ERR_NOMEM, "cudaMalloc of %llu bytes failed",
+                         (unsigned long long)(n * sizeof(T)));
+    }
+    b->allocs.push_back(v);
+    *p = (T *)v;
+    return HWC_OK;
+}
+
+static int batch_enqueue(hwc_batch *b, cudaStream_t s)
+{
+    const uint32_t nj = (uint32_t)b->jobs.size();
+    // the step's inputs: job descriptors and the work-item table, from pinned memory
+    HWC_CUDA_TRY(cudaMemcpyAsync(b->d_jobs, b->h_jobs, nj * sizeof(KJob), cudaMemcpyHostToDevice, s));
+    HWC_CUDA_TRY(cudaMemcpyAsync(b->d_item_start, b->h_item_start, (nj + 1) * sizeof(uint64_t),
+                                 cudaMemcpyHostToDevice, s));
+    int rc = launch_clear(b->d_jobs, nj, b->d_counter, s);
+    if (rc) return rc;
+    if (b->t0) HWC_CUDA_TRY(cudaEventRecordWithFlags(b->t0, s, cudaEventRecordExternal));
+    if (b->flags & HWC_FLAG_PLAIN) {
+        for (uint32_t i = 0; i < nj; ++i) {
+            rc = launch_plain(b->d_jobs + i, b->jobs[i].kj, b->shape, s);
+            if (rc) return rc;
+        }
+    } else {
+        rc = launch_persistent(b->d_jobs, b->d_item_start, nj, b->n_items, b->d_counter,
+                               b->max_smem, b->shape, s);
+        if (rc) return rc;
+    }
+    if (b->t1) HWC_CUDA_TRY(cudaEventRecordWithFlags(b->t1, s, cudaEventRecordExternal));
+    return launch_compact(b->d_jobs, nj, s);
+}
+
+// pick threads per CTA to maximise resident warps per SM for this smem size
+static int choose_shape(hwc_batch *b)
+{
+    const bool persistent = !(b->flags & HWC_FLAG_PLAIN);
+    const int sms = device_sm_count();
+    int best_block = 256, best_warps = -1, best_ctas = 1;
+    for (int block : {1024, 512, 256}) {
+        int ctas = 0;
+        int rc = max_ctas_per_sm(block, b->max_smem, persistent, &ctas);
+        if (rc) return rc;
+        int warps = ctas * block / 32;
+        if (warps > best_warps) {
+            best_warps = warps;
+            best_block = block;
+            best_ctas = ctas;
+        }
+    }
+    if (best_warps <= 0)
+        return set_error(HWC_ERR_TOO_LARGE, "no CTA fits %u bytes of shared memory", b->max_smem);
+    b->shape.block = best_block;
+    b->shape.grid = sms * best_ctas;
+    b->shape.item_tiles = (best_block / 32) * 2;
+    return HWC_OK;
+}
+
+static int batch_create_impl(const hwc_job_t *jobs, size_t n, uint32_t flags, uint32_t cap_scale,
+                             hwc_batch **out)
+{
+    *out = nullptr;
+    if (!jobs || n == 0) return set_error(HWC_ERR_ARG, "no jobs");
+    for (size_t i = 0; i < n; ++i) {   // argument errors before any CUDA call
+        uint64_t fam_n = 0;
+        int vrc = validate_job(jobs[i], &fam_n);
+        if (vrc) return vrc;
+    }
+    int rc = prepare_count_kernels();
+    if (rc) return rc;
+    hwc_batch *b = new hwc_batch();
+    b->flags = flags;
+    cudaGetDevice(&b->device);
+    b->jobs.resize(n);
+    for (size_t i = 0; i < n; ++i) {
+        HostJob &hj = b->jobs[i];
+        hj.job = jobs[i];
+        rc = fill_kjob(jobs[i], hj.kj, &hj.fam_n);
+        if (rc) { batch_release(b); return rc; }
+        KJob &kj = hj.kj;
+        const uint32_t cap = hash_capacity(kj.g, kj.q, jobs[i].count, cap_scale);
+        kj.hmask = cap - 1;
+        if ((rc = dalloc(b, &kj.hkeys, cap)) || (rc = dalloc(b, &kj.hcounts, cap)) ||
+            (rc = dalloc(b, &kj.stats, 4)) || (rc = dalloc(b, &kj.out_keys, cap)) ||
+            (rc = dalloc(b, &kj.out_counts, cap)) || (rc = dalloc(b, &kj.n_out, 1))) {
+            batch_release(b);
+            return rc;
+        }
+        b->max_smem = std::max(b->max_smem, kj.smem_bytes);
+    }
+    if ((rc = choose_shape(b))) { batch_release(b); return rc; }
+    // work items: each job is cut into items of item_tiles tiles, in job order
+    std::vector<uint64_t> starts(n + 1, 0);
+    for (size_t i = 0; i < n; ++i)
+        starts[i + 1] = starts[i] + (b->jobs[i].kj.n_tiles + b->shape.item_tiles - 1) / b->shape.item_tiles;
+    b->n_items = starts[n];
+    if ((rc = dalloc(b, &b->d_jobs, n)) || (rc = dalloc(b, &b->d_item_start, n + 1)) ||
+        (rc = dalloc(b, &b->d_counter, 1))) {
+        batch_release(b);
+        return rc;
+    }
+    if (cudaMallocHost(&b->h_jobs, n * sizeof(KJob)) != cudaSuccess ||
+        cudaMallocHost(&b->h_item_start, (n + 1) * sizeof(uint64_t)) != cudaSuccess) {
+        cudaGetLastError();
+        batch_release(b);
+        return set_error(HWC_ERR_NOMEM, "pinned host allocation failed");
+    }
+    for (size_t i = 0; i < n; ++i) b->h_jobs[i] = b->jobs[i].kj;
+    std::copy(starts.begin(), starts.end(), b->h_item_start);
+    if (flags & HWC_FLAG_TIMING) {
+        if (cudaEventCreate(&b->t0) != cudaSuccess || cudaEventCreate(&b->t1) != cudaSuccess) {
+            batch_release(b);
+            return set_error(HWC_ERR_CUDA, "cudaEventCreate failed");
+        }
+    }
+    b->launches_per_run = 2 + ((flags & HWC_FLAG_PLAIN) ? (uint32_t)n : 1u);
+    if (cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess) {
+        batch_release(b);
+        return set_error(HWC_ERR_CUDA, "cudaEventCreate failed");
+    }
+    if (flags & HWC_FLAG_GRAPH) {
+        cudaStream_t cs;
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+            batch_release(b);
+            return set_error(HWC_ERR_CUDA, "cudaStreamCreate failed");
+        }
+        cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (ce == cudaSuccess) {
+            rc = batch_enqueue(b, cs);
+            cudaError_t ce2 = cudaStreamEndCapture(cs, &b->graph);
+            if (rc == HWC_OK && ce2 == cudaSuccess)
+                ce = cudaGraphInstantiate(&b->gexec, b->graph, 0);
+            else if (ce2 != cudaSuccess)
+                ce = ce2;
+        }
+        cudaStreamDestroy(cs);
+        if (rc != HWC_OK || ce != cudaSuccess) {
+            batch_release(b);
+            return rc ? rc : set_error(HWC_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce));
+        }
+    }
+    *out = b;
+    return HWC_OK;
+}
+
+static int batch_result_impl(hwc_batch *b, size_t i, hwc_hist **out)
+{
+    *out = nullptr;
+    if (!b->launched) return set_error(HWC_ERR_STATE, "batch was not launched");
+    if (i >= b->jobs.size()) return set_error(HWC_ERR_ARG, "job %zu out of range", i);
+    HWC_CUDA_TRY(cudaEventSynchronize(b->done));
+    const KJob &kj = b->jobs[i].kj;
+    unsigned long long st[3] = {}, n_out = 0;
+    HWC_CUDA_TRY(cudaMemcpy(st, kj.stats, sizeof st, cudaMemcpyDeviceToHost));
+    HWC_CUDA_TRY(cudaMemcpy(&n_out, kj.n_out, sizeof n_out, cudaMemcpyDeviceToHost));
+    if (st[2]) return set_error(HWC_ERR_TOO_LARGE, "histogram hash of job %zu overflowed", i);
+    std::vector<unsigned long long> keys(n_out), cnt(n_out);
+    if (n_out) {
+        HWC_CUDA_TRY(cudaMemcpy(keys.data(), kj.out_keys, n_out * 8, cudaMemcpyDeviceToHost));
+        HWC_CUDA_TRY(cudaMemcpy(cnt.data(), kj.out_counts, n_out * 8, cudaMemcpyDeviceToHost));
+    }
+    if (i == 0) b->d2h_last = 0;
+    b->d2h_last += sizeof st + sizeof n_out + 16 * n_out;
+    hwc_hist *h = hist_from_keys(kj, keys.data(), cnt.data(), n_out, st[0]);
+    if (h->n_sqf != st[1]) {
+        uint64_t got = h->n_sqf;
+        delete h;
+        return set_error(HWC_ERR_CUDA, "histogram total %llu != square-free count %llu",
+                         (unsigned long long)got, (unsigned long long)st[1]);
+    }
+    *out = h;
+    return HWC_OK;
+}
+
+extern "C" int hwc_batch_create(const hwc_job_t *jobs, size_t n_jobs, uint32_t flags, hwc_batch_t **out)
+{
+    if (!out) return set_error(HWC_ERR_ARG, "out is NULL");
+    return batch_create_impl(jobs, n_jobs, flags, 1, out);
+}
+
+extern "C" int hwc_batch_launch(hwc_batch_t *b, void *stream)
+{
+    if (!b) return set_error(HWC_ERR_ARG, "batch is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (b->gexec) {
+        HWC_CUDA_TRY(cudaGraphLaunch(b->gexec, s));
+    } else {
+        int rc = batch_enqueue(b, s);
+        if (rc) return rc;
+    }
+    HWC_CUDA_TRY(cudaEventRecord(b->done, s));
+    b->launched = true;
+    return HWC_OK;
+}
+
+extern "C" int hwc_batch_result(hwc_batch_t *b, size_t i, hwc_hist_t **out)
+{
+    if (!b || !out) return set_error(HWC_ERR_ARG, "null argument");
+    return batch_result_impl(b, i, out);
+}
+
+extern "C" int hwc_batch_kernel_launches(const hwc_batch_t *b, uint32_t *n)
+{
+    if (!b || !n) return set_error(HWC_ERR_ARG, "null argument");
+    *n = b->launches_per_run;
+    return HWC_OK;
+}
+
+extern "C" int hwc_batch_io_bytes(const hwc_batch_t *b, uint64_t *h2d, uint64_t *d2h)
+{
+    if (!b) return set_error(HWC_ERR_ARG, "batch is NULL");
+    if (h2d) *h2d = b->jobs.size() * sizeof(KJob) + (b->jobs.size() + 1) * sizeof(uint64_t);
+    if (d2h) *d2h = b->d2h_last;
+    return HWC_OK;
+}
+
+extern "C" int hwc_batch_kernel_ms(hwc_batch_t *b, float *ms)
+{
+    if (!b || !ms) return set_error(HWC_ERR_ARG, "null argument");
+    if (!b->t0) return set_error(HWC_ERR_STATE, "batch created without HWC_FLAG_TIMING");
+    if (!b->launched) return set_error(HWC_ERR_STATE, "batch was not launched");
+    HWC_CUDA_TRY(cudaEventSynchronize(b->done));
+    HWC_CUDA_TRY(cudaEventElapsedTime(ms, b->t0, b->t1));
+    return HWC_OK;
+}
+
+extern "C" void hwc_batch_free(hwc_batch_t *b)
+{
+    if (b && b->launched) cudaEventSynchronize(b->done);
+    batch_release(b);
+}
+
+extern "C" int hwc_batch_run(const hwc_job_t *jobs, size_t n_jobs, uint32_t flags, void *stream,
+                             hwc_hist_t **outs)
+{
+    if (!outs) return set_error(HWC_ERR_ARG, "outs is NULL");
+    for (size_t i = 0; i < n_jobs; ++i) outs[i] = nullptr;
+    hwc_batch *b = nullptr;
+    int rc = HWC_OK;
+    for (uint32_t scale = 1; scale <= 64; scale *= 8) {
+        rc = batch_create_impl(jobs, n_jobs, flags, scale, &b);
+        if (rc) return rc;
+        rc = hwc_batch_launch(b, stream);
+        for (size_t i = 0; rc == HWC_OK && i < n_jobs; ++i) rc = batch_result_impl(b, i, &outs[i]);
+        hwc_batch_free(b);
+        if (rc != HWC_ERR_TOO_LARGE) break;
+        for (size_t i = 0; i < n_jobs; ++i) { hwc_hist_free(outs[i]); outs[i] = nullptr; }
+    }
+    if (rc) {
+        for (size_t i = 0; i < n_jobs; ++i) { hwc_hist_free(outs[i]); outs[i] = nullptr; }
+    }
+    return rc;
+}
+
+// ---------------------------------------------------------------------
+// single job
+
+extern "C" int hwc_family_size(uint32_t q, const hwc_family_t *fam, uint64_t *n)
+{
+    if (!n) return set_error(HWC_ERR_ARG, "n is NULL");
+    return family_size(q, fam, n);
+}
+
+extern "C" int hwc_count(uint32_t g, uint32_t q, const hwc_family_t *fam, uint64_t first,
+                         uint64_t count, uint32_t flags, void *stream, hwc_hist_t **out)
+{
+    if (!out || !fam) return set_error(HWC_ERR_ARG, "null argument");
+    *out = nullptr;
+    hwc_job_t j{};
+    j.g = g;
+    j.q = q;
+    j.family = *fam;
+    j.first = first;
+    j.count = count;
+    return hwc_batch_run(&j, 1, flags | HWC_FLAG_PLAIN, stream, out);
+}
+
+extern "C" int hwc_count_members(uint32_t g, uint32_t q, const hwc_family_t *fam, uint64_t first,
+                                 uint64_t count, int unfiltered, void *stream, int32_t *counts,
+                                 uint8_t *sqf)
+{
+    if (!fam || (count && (!counts || !sqf))) return set_error(HWC_ERR_ARG, "null argument");
+    hwc_job_t j{};
+    j.g = g;
+    j.q = q;
+    j.family = *fam;
+    j.first = first;
+    j.count = count;
+    uint64_t fam_n = 0;
+    int rc = validate_job(j, &fam_n);
+    if (rc) return rc;
+    rc = prepare_count_kernels();
+    if (rc) return rc;
+    KJob kj;
+    rc = fill_kjob(j, kj, &fam_n);
+    if (rc) return rc;
+    if (count == 0) return HWC_OK;
+    kj.unfiltered = unfiltered ? 1u : 0u;
+    cudaStream_t s = (cudaStream_t)stream;
+    hwc_batch *b = new hwc_batch();   // allocation holder only
+    if ((rc = dalloc(b, &kj.member_counts, count * g)) || (rc = dalloc(b, &kj.member_sqf, count)) ||
+        (rc = dalloc(b, &kj.stats, 4)) || (rc = dalloc(b, &b->d_jobs, 1))) {
+        batch_release(b);
+        return rc;
+    }
+    cudaError_t ce = cudaMemsetAsync(kj.stats, 0, 4 * sizeof(unsigned long long), s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(b->d_jobs, &kj, sizeof kj, cudaMemcpyHostToDevice, s);
+    if (ce != cudaSuccess) {
+        batch_release(b);
+        return set_error(HWC_ERR_CUDA, "setup: %s", cudaGetErrorString(ce));
+    }
+    LaunchShape sh;
+    sh.block = 256;
+    int ctas = 0;
+    rc = max_ctas_per_sm(sh.block, kj.smem_bytes, false, &ctas);
+    if (rc == HWC_OK && ctas <= 0) rc = set_error(HWC_ERR_TOO_LARGE, "no CTA fits");
+    if (rc == HWC_OK) {
+        sh.grid = device_sm_count() * ctas;
+        rc = launch_plain(b->d_jobs, kj, sh, s);
+    }
+    if (rc == HWC_OK) {
+        ce = cudaMemcpyAsync(counts, kj.member_counts, count * g * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(sqf, kj.member_sqf, count, cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess) rc = set_error(HWC_ERR_CUDA, "per-member run: %s", cudaGetErrorString(ce));
+    }
+    batch_release(b);
+    return rc;
+}
+
+// ---------------------------------------------------------------------
+// histogram ABI
+
+extern "C" int hwc_hist_size(const hwc_hist_t *h, uint64_t *n_entries, uint64_t *n_squarefree,
+                             uint64_t *n_total)
+{
+    if (!h) return set_error(HWC_ERR_ARG, "histogram is NULL");
+    if (n_entries) *n_entries = h->mult.size();
+    if (n_squarefree) *n_squarefree = h->n_sqf;
+    if (n_total) *n_total = h->n_total;
+    return HWC_OK;
+}
+
+extern "C" int hwc_hist_genus(const hwc_hist_t *h, uint32_t *g)
+{
+    if (!h || !g) return set_error(HWC_ERR_ARG, "null argument");
+    *g = h->g;
+    return HWC_OK;
+}
+
+extern "C" int hwc_hist_read(const hwc_hist_t *h, int32_t *counts, uint64_t *mult)
+{
+    if (!h) return set_error(HWC_ERR_ARG, "histogram is NULL");
+    if (counts && !h->counts.empty()) std::memcpy(counts, h->counts.data(), h->counts.size() * sizeof(int32_t));
+    if (mult && !h->mult.empty()) std::memcpy(mult, h->mult.data(), h->mult.size() * sizeof(uint64_t));
+    return HWC_OK;
+}
+
+extern "C" int hwc_hist_merge(hwc_hist_t *into, const hwc_hist_t *from)
+{
+    if (!into || !from) return set_error(HWC_ERR_ARG, "histogram is NULL");
+    if (into->g != from->g) return set_error(HWC_ERR_ARG, "genus mismatch %u vs %u", into->g, from->g);
+    const uint32_t g = into->g;
+    std::map<std::vector<int32_t>, uint64_t> m;
+    for (const hwc_hist *h : {(const hwc_hist *)into, from})
+        for (size_t i = 0; i < h->mult.size(); ++i)
+            m[std::vector<int32_t>(&h->counts[i * g], &h->counts[i * g] + g)] += h->mult[i];
+    hwc_hist *r = hist_from_map(g, m, into->n_total + from->n_total);
+    std::swap(*into, *r);
+    delete r;
+    return HWC_OK;
+}
+
+extern "C" int hwc_hist_from_arrays(uint32_t g, uint64_t n_entries, const int32_t *counts,
+                                    const uint64_t *mult, uint64_t n_total, hwc_hist_t **out)
+{
+    if (!out || (n_entries && (!counts || !mult)) || g < 1 || g > (uint32_t)kMaxG)
+        return set_error(HWC_ERR_ARG, "bad argument");
+    std::map<std::vector<int32_t>, uint64_t> m;
+    for (uint64_t i = 0; i < n_entries; ++i)
+        m[std::vector<int32_t>(counts + i * g, counts + i * g + g)] += mult[i];
+    *out = hist_from_map(g, m, n_total);
+    return HWC_OK;
+}
+
+extern "C" void hwc_hist_free(hwc_hist_t *h)
+{
+    delete h;
+}
+
+extern "C" const char *hwc_last_error(void)
+{
+    return hwc::g_err.c_str();
+}
+
+extern "C" const char *hwc_version(void)
+{
+    return "hwc 0.1 sm_103a";
+}

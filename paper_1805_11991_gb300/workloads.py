@@ -1,0 +1,101 @@
+"""Seeded synthetic workloads: the five benchmark configurations.
+
+Job lists only (family, index range, sampling seed) and the Poisson arrival
+schedule of the served configuration.  Nothing here computes any part of the
+point count; the GPU library and the oracle each decode these descriptions on
+their own.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+ALL_DEG, MONIC_NOSUB, MONIC_NOSUB_SAMPLED = 0, 1, 2
+
+# odd prime powers below 64
+ODD_PRIME_POWERS_BELOW_64 = [3, 5, 7, 9, 11, 13, 17, 19, 23, 25, 27, 29, 31, 37, 41, 43, 47, 49,
+                             53, 59, 61]
+
+
+@dataclass(frozen=True)
+class JobSpec:
+    g: int
+    q: int
+    kind: int
+    degree: int
+    first: int = 0
+    count: int = -1          # -1: the whole family
+    seed: int = 0
+    sample_count: int = 0
+
+    def family_members(self) -> int:
+        if self.kind == ALL_DEG:
+            return (self.q - 1) * self.q ** self.degree
+        if self.kind == MONIC_NOSUB:
+            return self.q ** (self.degree - 1)
+        return self.sample_count
+
+    def n(self) -> int:
+        return self.family_members() - self.first if self.count < 0 else self.count
+
+    def nominal_evals_per_member(self) -> int:
+        """Points x in F_{q^k}, k = 1..g, each member is evaluated at."""
+        return sum(self.q ** k for k in range(1, self.g + 1))
+
+    def with_range(self, first: int, count: int) -> "JobSpec":
+        return JobSpec(self.g, self.q, self.kind, self.degree, first, count, self.seed, self.sample_count)
+
+
+def config1():
+    """g=2, q=3: every f of exact degree 5 or 6 (486 + 1458 members)."""
+    return [JobSpec(2, 3, ALL_DEG, 5), JobSpec(2, 3, ALL_DEG, 6)]
+
+
+def config2():
+    """g=2, q=31 and q=27: full monic degree-5 and -6 families with c_{d-1}=0."""
+    return [JobSpec(2, q, MONIC_NOSUB, d) for q in (31, 27) for d in (5, 6)]
+
+
+def config3():
+    """g=2, every odd prime power q<64 (full monic degree-5, c_4=0) plus q=293
+    with 2^24 members drawn by seed 7."""
+    jobs = [JobSpec(2, q, MONIC_NOSUB, 5) for q in ODD_PRIME_POWERS_BELOW_64]
+    jobs.append(JobSpec(2, 293, MONIC_NOSUB_SAMPLED, 5, seed=7, sample_count=1 << 24))
+    return jobs
+
+
+def config4():
+    """g=3, q in {13, 17, 25, 27}: full monic degree-7 families with c_6=0."""
+    return [JobSpec(3, q, MONIC_NOSUB, 7) for q in (13, 17, 25, 27)]
+
+
+def config5():
+    """g=4 served: full monic degree-9 (c_8=0) families for q in {7, 9, 11} and
+    q=13 with 2^26 members drawn by seed 11."""
+    jobs = [JobSpec(4, q, MONIC_NOSUB, 9) for q in (7, 9, 11)]
+    jobs.append(JobSpec(4, 13, MONIC_NOSUB_SAMPLED, 9, seed=11, sample_count=1 << 26))
+    return jobs
+
+
+CONFIGS = {"config1": config1, "config2": config2, "config3": config3, "config4": config4,
+           "config5": config5}
+
+
+def poisson_arrivals(n: int, rate_per_s: float, seed: int = 11) -> np.ndarray:
+    """Arrival times (s) of n requests of a Poisson process (exponential gaps)."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate_per_s, size=n))
+
+
+def split_job(job: JobSpec, parts: int):
+    """Cut a job's member range into `parts` contiguous slices (serving requests,
+    shards)."""
+    n = job.n()
+    out = []
+    for i in range(parts):
+        a = job.first + (n * i) // parts
+        b = job.first + (n * (i + 1)) // parts
+        if b > a:
+            out.append(job.with_range(a, b - a))
+    return out
