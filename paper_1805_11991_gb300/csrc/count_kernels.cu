@@ -167,10 +167,16 @@ __device__ bool squarefree(const FqLog<Tab> &F, const uint32_t *coef1, uint32_t 
 
 // ---------------------------------------------------------------------
 // one field: sum over x in F_Q^x of chi(f(x)) for this lane's share of x
+//
+// Two table layouts: TRIPLE (entries over [0, 3L], poison 3L) lets a step be
+// u <- min(T[u] + d + g*j, 3L) with d, g*j < L and no reduction; DOUBLE
+// (entries over [0, 2L], poison 2L) reduces d + g*j mod L first.
 
+// Horner in the log domain with explicit zero handling, for the rare x at
+// which some partial sum vanishes (the chain above then holds the poison).
 template <int D, class Tab>
-__device__ __noinline__ int slow_chi(const Tab T, uint32_t L, const uint32_t (&lam)[D + 1],
-                                     uint32_t nz, uint32_t j)
+__device__ __forceinline__ int slow_chi(const Tab T, uint32_t L, uint32_t cap,
+                                        const uint32_t (&lam)[D + 1], uint32_t nz, uint32_t j)
 {
     uint32_t l = lam[D];
     bool zero = false;
@@ -182,9 +188,9 @@ __device__ __noinline__ int slow_chi(const Tab T, uint32_t L, const uint32_t (&l
                 l = lam[i];
                 zero = false;
             } else {
-                uint32_t n = addmod(l, L - lam[i], L);
-                uint32_t z = T[n];
-                if (z >= 2 * L) zero = true;
+                const uint32_t n = addmod(l, L - lam[i], L);
+                const uint32_t z = T[n];
+                if (z >= cap) zero = true;
                 else l = addmod(lam[i], z, L);
             }
         }
@@ -192,11 +198,32 @@ __device__ __noinline__ int slow_chi(const Tab T, uint32_t L, const uint32_t (&l
     return zero ? 0 : ((l & 1u) ? -1 : 1);
 }
 
-template <int D, class Tab>
+template <bool TRIPLE>
+__device__ __forceinline__ uint32_t chain_step(uint32_t z, uint32_t d, uint32_t m, uint32_t L, uint32_t cap)
+{
+    if (TRIPLE) return min(z + d + m, cap);
+    return min(z + addmod(d, m, L), cap);
+}
+
+// dense chain: every coefficient below position I1 is nonzero (all gaps 1)
+template <int D, int I1, bool TRIPLE, class Tab>
+__device__ __forceinline__ void dense_chain(const Tab T, const uint32_t (&dli)[D], uint32_t L,
+                                            uint32_t cap, uint32_t xA, uint32_t xB,
+                                            uint32_t &uA, uint32_t &uB)
+{
+#pragma unroll
+    for (int i = I1 - 1; i >= 0; --i) {
+        const uint32_t zA = T[uA], zB = T[uB];
+        uA = chain_step<TRIPLE>(zA, dli[i], xA, L, cap);
+        uB = chain_step<TRIPLE>(zB, dli[i], xB, L, cap);
+    }
+}
+
+template <int D, bool TRIPLE, class Tab>
 __device__ __forceinline__ int field_chi_sum(const Tab T, uint32_t L, uint32_t bar,
                                              const uint32_t (&lam)[D + 1], uint32_t nz, int lane)
 {
-    const uint32_t L2 = 2 * L;
+    const uint32_t cap = TRIPLE ? 3 * L : 2 * L;
     int S = 0;
     if (nz == 0) {   // f = c_D x^D
         for (uint32_t j = lane; j < L; j += 32) S += ((lam[D] + (uint32_t)D * j) & 1u) ? -1 : 1;
@@ -205,44 +232,75 @@ __device__ __forceinline__ int field_chi_sum(const Tab T, uint32_t L, uint32_t b
     const int i1 = 31 - __clz(nz);
     const int is = __ffs(nz) - 1;
     const uint32_t g1 = (uint32_t)(D - i1);
-    const uint32_t negl1 = L - lam[i1];
-    const uint32_t lamlast = lam[is];
-    for (uint32_t j0 = 0; j0 < L; j0 += 64) {
-        uint32_t jA = j0 + lane, jB = j0 + 32 + lane;
-        const bool vA = jA < L, vB = jB < L;
-        jA = vA ? jA : 0;
-        jB = vB ? jB : 0;
-        uint32_t uA = addmod(lam[D], mulmod_small(g1, jA, L, bar), L) + negl1;
-        uint32_t uB = addmod(lam[D], mulmod_small(g1, jB, L, bar), L) + negl1;
+    // first step index: lam_D + g1*j - lam_{i1}, kept in [0, 2L)
+    const uint32_t base1 = lam[D] + (L - lam[i1]);     // < 2L
+    const uint32_t lam_last = lam[is];
+    const uint32_t is_odd = (uint32_t)is & 1u;
+    // per-position constants of the chain (static indices: registers)
+    uint32_t dli[D], gpi[D];
+    {
         uint32_t lp = lam[i1];
         int ip = i1;
 #pragma unroll
-        for (int i = D - 2; i >= 0; --i) {
-            if (i >= i1 || !((nz >> i) & 1u)) continue;
-            const uint32_t dl = addmod(lp, L - lam[i], L);
-            const uint32_t gap = (uint32_t)(ip - i);
-            uint32_t eA, eB;
-            if (gap == 1) {
-                eA = addmod(dl, jA, L);
-                eB = addmod(dl, jB, L);
-            } else {
-                eA = addmod(dl, mulmod_small(gap, jA, L, bar), L);
-                eB = addmod(dl, mulmod_small(gap, jB, L, bar), L);
+        for (int i = D - 1; i >= 0; --i) {
+            dli[i] = 0;
+            gpi[i] = 0;
+            if (i < i1 && ((nz >> i) & 1u)) {
+                dli[i] = addmod(lp, L - lam[i], L);
+                gpi[i] = (uint32_t)(ip - i);
+                lp = lam[i];
+                ip = i;
             }
-            const uint32_t zA = T[uA], zB = T[uB];
-            uA = min(zA + eA, L2);
-            uB = min(zB + eB, L2);
-            lp = lam[i];
-            ip = i;
+        }
+    }
+    // dense patterns get a branch-free chain
+    const int dense = (nz == (1u << (D - 1)) - 1u) ? 2 : (nz == (1u << D) - 1u) ? 1 : 0;
+    for (uint32_t j0 = 0; j0 < L; j0 += 64) {
+        const uint32_t jA = j0 + lane, jB = j0 + 32 + lane;
+        const bool vA = jA < L, vB = jB < L;
+        const uint32_t xA = vA ? jA : 0, xB = vB ? jB : 0;
+        uint32_t mA, mB;
+        if (g1 == 2) {   // lead at D, first nonzero at D-2: 2j mod L
+            mA = min(2 * xA, 2 * xA - L);
+            mB = min(2 * xB, 2 * xB - L);
+        } else {
+            mA = mulmod_small(g1, xA, L, bar);
+            mB = mulmod_small(g1, xB, L, bar);
+        }
+        uint32_t uA = base1 + mA, uB = base1 + mB;       // < 3L
+        if (!TRIPLE) {
+            uA = min(uA, uA - L);                          // unsigned: back below 2L
+            uB = min(uB, uB - L);
+        }
+        if (dense == 2) {
+            dense_chain<D, D - 2, TRIPLE>(T, dli, L, cap, xA, xB, uA, uB);
+        } else if (dense == 1) {
+            dense_chain<D, D - 1, TRIPLE>(T, dli, L, cap, xA, xB, uA, uB);
+        } else {
+#pragma unroll
+            for (int i = D - 2; i >= 0; --i) {
+                if (gpi[i] == 0) continue;                 // zero coefficient or above i1
+                uint32_t sA, sB;
+                if (gpi[i] == 1) {
+                    sA = xA;
+                    sB = xB;
+                } else {
+                    sA = mulmod_small(gpi[i], xA, L, bar);
+                    sB = mulmod_small(gpi[i], xB, L, bar);
+                }
+                const uint32_t zA = T[uA], zB = T[uB];
+                uA = chain_step<TRIPLE>(zA, dli[i], sA, L, cap);
+                uB = chain_step<TRIPLE>(zB, dli[i], sB, L, cap);
+            }
         }
         const uint32_t zA = T[uA], zB = T[uB];
-        const uint32_t tailA = (uint32_t)is * jA, tailB = (uint32_t)is * jB;
-        int cA = ((lamlast + zA + tailA) & 1u) ? -1 : 1;
-        int cB = ((lamlast + zB + tailB) & 1u) ? -1 : 1;
-        const bool pA = vA && zA >= L2, pB = vB && zB >= L2;
+        // f(x) = alpha^(lam_last + z + is*j): chi is the parity of the exponent
+        int cA = 1 - 2 * (int)((lam_last ^ zA ^ (xA & is_odd)) & 1u);
+        int cB = 1 - 2 * (int)((lam_last ^ zB ^ (xB & is_odd)) & 1u);
+        const bool pA = vA && zA >= cap, pB = vB && zB >= cap;
         if (__any_sync(kFull, pA || pB)) {
-            if (pA) cA = slow_chi<D>(T, L, lam, nz, jA);
-            if (pB) cB = slow_chi<D>(T, L, lam, nz, jB);
+            if (pA) cA = slow_chi<D>(T, L, cap, lam, nz, xA);
+            if (pB) cB = slow_chi<D>(T, L, cap, lam, nz, xB);
         }
         S += (vA ? cA : 0) + (vB ? cB : 0);
     }
@@ -293,7 +351,7 @@ __device__ void process_tile(const KJob &J, uint64_t tile, const uint8_t *smem, 
     bool sqf = false;
     if (valid) {
         const uint32_t *coef1 = s32 + J.coef_off[0];
-        if (J.tab_off[0] != kWideTable) {
+        if (J.tab_kind[0] != kTabDoubleGlobal) {
             FqLog<TabS> F{TabS{s16 + J.tab_off[0]}, J.L[0]};
             sqf = squarefree<D>(F, coef1, J.p, c);
         } else {
@@ -330,10 +388,13 @@ __device__ void process_tile(const KJob &J, uint64_t tile, const uint8_t *smem, 
 #pragma unroll
             for (int i = 0; i <= D; ++i) lam[i] = coefk[cc[i]];
             int S;
-            if (J.tab_off[k] != kWideTable)
-                S = field_chi_sum<D>(TabS{s16 + J.tab_off[k]}, L, J.barrett[k], lam, nz, lane);
+            const uint32_t kind = J.tab_kind[k];
+            if (kind == kTabTripleSmem)
+                S = field_chi_sum<D, true>(TabS{s16 + J.tab_off[k]}, L, J.barrett[k], lam, nz, lane);
+            else if (kind == kTabDoubleSmem)
+                S = field_chi_sum<D, false>(TabS{s16 + J.tab_off[k]}, L, J.barrett[k], lam, nz, lane);
             else
-                S = field_chi_sum<D>(TabG{J.zech2w[k]}, L, J.barrett[k], lam, nz, lane);
+                S = field_chi_sum<D, false>(TabG{J.zech2w[k]}, L, J.barrett[k], lam, nz, lane);
             if (lane == 0 && cc[0] != 0) S += (lam[0] & 1u) ? -1 : 1;   // x = 0
             S = __reduce_add_sync(kFull, S);
             // points at infinity: 1 + chi(c_{2g+2})
@@ -363,31 +424,16 @@ __device__ void process_tile(const KJob &J, uint64_t tile, const uint8_t *smem, 
     }
 }
 
-__device__ void process_tile_any(const KJob &J, uint64_t tile, const uint8_t *smem, int lane,
-                                 WarpStats &st)
-{
-    switch (J.d) {
-    case 3: process_tile<3>(J, tile, smem, lane, st); break;
-    case 4: process_tile<4>(J, tile, smem, lane, st); break;
-    case 5: process_tile<5>(J, tile, smem, lane, st); break;
-    case 6: process_tile<6>(J, tile, smem, lane, st); break;
-    case 7: process_tile<7>(J, tile, smem, lane, st); break;
-    case 8: process_tile<8>(J, tile, smem, lane, st); break;
-    case 9: process_tile<9>(J, tile, smem, lane, st); break;
-    case 10: process_tile<10>(J, tile, smem, lane, st); break;
-    default: break;
-    }
-}
-
 // copy the job's tables into shared memory (all threads of the CTA)
 __device__ void stage_job(const KJob &J, uint8_t *smem)
 {
     uint16_t *s16 = reinterpret_cast<uint16_t *>(smem);
     uint32_t *s32 = reinterpret_cast<uint32_t *>(smem);
     for (uint32_t k = 0; k < J.g; ++k) {
-        if (J.tab_off[k] != kWideTable) {
-            const uint32_t n = 2 * J.L[k] + 1;
-            const uint16_t *src = J.zech2[k];
+        if (J.tab_kind[k] != kTabDoubleGlobal) {
+            const bool tri = J.tab_kind[k] == kTabTripleSmem;
+            const uint32_t n = (tri ? 3 : 2) * J.L[k] + 1;
+            const uint16_t *src = tri ? J.zech3[k] : J.zech2[k];
             uint16_t *dst = s16 + J.tab_off[k];
             for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
         }
@@ -409,7 +455,8 @@ __device__ __forceinline__ void flush_stats(const KJob &J, WarpStats &st, int la
 // ---------------------------------------------------------------------
 // kernels
 
-__global__ void k_plain(const KJob *__restrict__ jp)
+template <int D>
+__global__ void __launch_bounds__(256) k_plain(const KJob *__restrict__ jp)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     const KJob &J = *jp;
@@ -418,13 +465,17 @@ __global__ void k_plain(const KJob *__restrict__ jp)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     WarpStats st;
     for (uint64_t t = (uint64_t)blockIdx.x * nw + warp; t < J.n_tiles; t += (uint64_t)gridDim.x * nw)
-        process_tile_any(J, t, smem, lane, st);
+        process_tile<D>(J, t, smem, lane, st);
     flush_stats(J, st, lane);
 }
 
-__global__ void k_persistent(const KJob *__restrict__ jobs, const uint64_t *__restrict__ item_start,
-                             uint32_t n_jobs, uint64_t n_items, unsigned long long *counter,
-                             uint32_t item_tiles)
+// Persistent: CTAs pull work items (a run of tiles of one job) from a counter
+// until the queue is empty; a CTA restages tables only when its job changes.
+template <int D>
+__global__ void __launch_bounds__(256) k_persistent(const KJob *__restrict__ jobs,
+                                                    const uint64_t *__restrict__ item_start,
+                                                    uint32_t n_jobs, uint64_t n_items,
+                                                    unsigned long long *counter, uint32_t item_tiles)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ unsigned long long s_item;
@@ -440,7 +491,7 @@ __global__ void k_persistent(const KJob *__restrict__ jobs, const uint64_t *__re
         // job owning this item: item_start is ascending, item_start[n_jobs] = n_items
         uint32_t lo = 0, hi = n_jobs;
         while (hi - lo > 1) {
-            uint32_t mid = (lo + hi) >> 1;
+            const uint32_t mid = (lo + hi) >> 1;
             if (item_start[mid] <= item) lo = mid;
             else hi = mid;
         }
@@ -454,16 +505,18 @@ __global__ void k_persistent(const KJob *__restrict__ jobs, const uint64_t *__re
         const KJob &J = jobs[jb];
         const uint64_t t0 = (item - item_start[jb]) * item_tiles;
         const uint64_t t1 = min(t0 + item_tiles, J.n_tiles);
-        for (uint64_t t = t0 + warp; t < t1; t += nw) process_tile_any(J, t, smem, lane, st);
+        for (uint64_t t = t0 + warp; t < t1; t += nw) process_tile<D>(J, t, smem, lane, st);
         __syncthreads();   // tables may be restaged next iteration
     }
     if (cur >= 0) flush_stats(jobs[cur], st, lane);
 }
 
-__global__ void k_clear(const KJob *__restrict__ jobs, uint32_t n_jobs, unsigned long long *counter)
+__global__ void k_clear(const KJob *__restrict__ jobs, uint32_t n_jobs, unsigned long long *counters,
+                        uint32_t n_counters)
 {
     const uint32_t jb = blockIdx.y;
-    if (jb == 0 && blockIdx.x == 0 && threadIdx.x == 0 && counter) *counter = 0;
+    if (jb == 0 && blockIdx.x == 0 && counters)
+        for (uint32_t i = threadIdx.x; i < n_counters; i += blockDim.x) counters[i] = 0;
     if (jb >= n_jobs) return;
     const KJob &J = jobs[jb];
     if (blockIdx.x == 0 && threadIdx.x < 4) {
@@ -508,6 +561,38 @@ __global__ void k_compact(const KJob *__restrict__ jobs, uint32_t n_jobs)
 // ---------------------------------------------------------------------
 // host launch wrappers
 
+using KernelFn = const void *;
+
+static KernelFn plain_fn(int D)
+{
+    switch (D) {
+    case 3: return (KernelFn)k_plain<3>;
+    case 4: return (KernelFn)k_plain<4>;
+    case 5: return (KernelFn)k_plain<5>;
+    case 6: return (KernelFn)k_plain<6>;
+    case 7: return (KernelFn)k_plain<7>;
+    case 8: return (KernelFn)k_plain<8>;
+    case 9: return (KernelFn)k_plain<9>;
+    case 10: return (KernelFn)k_plain<10>;
+    default: return nullptr;
+    }
+}
+
+static KernelFn persistent_fn(int D)
+{
+    switch (D) {
+    case 3: return (KernelFn)k_persistent<3>;
+    case 4: return (KernelFn)k_persistent<4>;
+    case 5: return (KernelFn)k_persistent<5>;
+    case 6: return (KernelFn)k_persistent<6>;
+    case 7: return (KernelFn)k_persistent<7>;
+    case 8: return (KernelFn)k_persistent<8>;
+    case 9: return (KernelFn)k_persistent<9>;
+    case 10: return (KernelFn)k_persistent<10>;
+    default: return nullptr;
+    }
+}
+
 int prepare_count_kernels(void)
 {
     static std::mutex mu;
@@ -517,8 +602,14 @@ int prepare_count_kernels(void)
     std::lock_guard<std::mutex> lk(mu);
     if (dev >= 0 && dev < 64 && done[dev]) return HWC_OK;
     const int optin = (int)device_smem_optin();
-    HWC_CUDA_TRY(cudaFuncSetAttribute((const void *)k_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-    HWC_CUDA_TRY(cudaFuncSetAttribute((const void *)k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    for (int D = 3; D <= kMaxD; ++D) {
+        for (KernelFn fn : {plain_fn(D), persistent_fn(D)}) {
+            cudaFuncAttributes fa{};
+            HWC_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));   // static smem counts against the limit
+            HWC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              optin - (int)fa.sharedSizeBytes));
+        }
+    }
     if (dev >= 0 && dev < 64) done[dev] = true;
     return HWC_OK;
 }
@@ -539,19 +630,21 @@ uint32_t device_smem_optin(void)
     return n > 0 ? (uint32_t)n : 48u * 1024u;
 }
 
-int max_ctas_per_sm(int block, uint32_t smem_bytes, bool persistent, int *out)
+int max_ctas_per_sm(int D, int block, uint32_t smem_bytes, bool persistent, int *out)
 {
     int n = 0;
-    const void *fn = persistent ? (const void *)k_persistent : (const void *)k_plain;
+    KernelFn fn = persistent ? persistent_fn(D) : plain_fn(D);
+    if (!fn) return set_error(HWC_ERR_ARG, "degree %d has no kernel", D);
     HWC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, smem_bytes));
     *out = n;
     return HWC_OK;
 }
 
-int launch_clear(const KJob *d_jobs, uint32_t n_jobs, unsigned long long *d_counter, cudaStream_t s)
+int launch_clear(const KJob *d_jobs, uint32_t n_jobs, unsigned long long *d_counters,
+                 uint32_t n_counters, cudaStream_t s)
 {
     dim3 grid(device_sm_count(), std::max<uint32_t>(n_jobs, 1));
-    k_clear<<<grid, 256, 0, s>>>(d_jobs, n_jobs, d_counter);
+    k_clear<<<grid, 256, 0, s>>>(d_jobs, n_jobs, d_counters, n_counters);
     HWC_CUDA_TRY(cudaGetLastError());
     return HWC_OK;
 }
@@ -560,20 +653,25 @@ int launch_plain(const KJob *d_job, const KJob &h_job, const LaunchShape &sh, cu
 {
     int grid = sh.grid;
     if (grid <= 0) grid = device_sm_count();
-    uint64_t need = (h_job.n_tiles + (sh.block / 32) - 1) / (sh.block / 32);
+    const uint64_t need = (h_job.n_tiles + (sh.block / 32) - 1) / (sh.block / 32);
     if ((uint64_t)grid > need) grid = (int)std::max<uint64_t>(need, 1);
-    k_plain<<<grid, sh.block, h_job.smem_bytes, s>>>(d_job);
-    HWC_CUDA_TRY(cudaGetLastError());
+    KernelFn fn = plain_fn((int)h_job.d);
+    if (!fn) return set_error(HWC_ERR_ARG, "degree %u has no kernel", h_job.d);
+    void *args[] = {(void *)&d_job};
+    HWC_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(sh.block), args, h_job.smem_bytes, s));
     return HWC_OK;
 }
 
-int launch_persistent(const KJob *d_jobs, const uint64_t *d_item_start, uint32_t n_jobs,
+int launch_persistent(int D, const KJob *d_jobs, const uint64_t *d_item_start, uint32_t n_jobs,
                       uint64_t n_items, unsigned long long *d_counter, uint32_t max_smem,
                       const LaunchShape &sh, cudaStream_t s)
 {
-    k_persistent<<<sh.grid, sh.block, max_smem, s>>>(d_jobs, d_item_start, n_jobs, n_items, d_counter,
-                                                    (uint32_t)sh.item_tiles);
-    HWC_CUDA_TRY(cudaGetLastError());
+    KernelFn fn = persistent_fn(D);
+    if (!fn) return set_error(HWC_ERR_ARG, "degree %d has no kernel", D);
+    uint32_t item_tiles = (uint32_t)sh.item_tiles;
+    void *args[] = {(void *)&d_jobs, (void *)&d_item_start, (void *)&n_jobs, (void *)&n_items,
+                    (void *)&d_counter, (void *)&item_tiles};
+    HWC_CUDA_TRY(cudaLaunchKernel(fn, dim3(sh.grid), dim3(sh.block), args, max_smem, s));
     return HWC_OK;
 }
 

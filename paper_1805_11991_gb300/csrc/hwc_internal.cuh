@@ -52,6 +52,17 @@ struct Tables {
     // value 2L, and entry 2L = 2L (absorbing).  u16 when 2L < 65536.
     uint16_t *d_zech2 = nullptr;    // [2L+1] or null
     uint32_t *d_zech2w = nullptr;   // [2L+1]
+    // tripled layout: entry u in [0, 3L) is Z[u mod L] (poison 3L), T[3L] = 3L;
+    // a step index z + d + j with z, d, j < L needs no reduction.  u16 when
+    // 3L < 65536.
+    uint16_t *d_zech3 = nullptr;    // [3L+1] or null
+};
+
+// where a count kernel reads the Zech table of one field
+enum TabKind : uint32_t {
+    kTabTripleSmem = 0,   // d_zech3 staged in shared memory
+    kTabDoubleSmem = 1,   // d_zech2 staged in shared memory
+    kTabDoubleGlobal = 2, // d_zech2w read from global memory (L1/L2)
 };
 
 int tables_build(uint32_t q, uint32_t k, Tables **out);
@@ -73,8 +84,10 @@ struct KJob {
     uint64_t n_tiles;                 // ceil(count / 32)
     uint32_t Q[kMaxG], L[kMaxG];
     uint32_t barrett[kMaxG];          // floor(2^32 / L)
-    uint32_t tab_off[kMaxG];          // u16 offset of zech2 in smem or kWideTable
+    uint32_t tab_off[kMaxG];          // u16 offset of the table in smem (smem kinds)
+    uint32_t tab_kind[kMaxG];         // TabKind
     uint32_t coef_off[kMaxG];         // u32 offset of coef_log in smem (after tables)
+    const uint16_t *zech3[kMaxG];
     const uint16_t *zech2[kMaxG];
     const uint32_t *zech2w[kMaxG];
     const uint32_t *coef_log[kMaxG];
@@ -98,15 +111,17 @@ struct LaunchShape {
     int grid = 0;          // CTAs (0 = derive)
     int item_tiles = 4;    // tiles per queue item (persistent)
 };
-int launch_clear(const KJob *d_jobs, uint32_t n_jobs, unsigned long long *d_counter, cudaStream_t s);
+int launch_clear(const KJob *d_jobs, uint32_t n_jobs, unsigned long long *d_counters,
+                 uint32_t n_counters, cudaStream_t s);
 int launch_plain(const KJob *d_job, const KJob &h_job, const LaunchShape &sh, cudaStream_t s);
-int launch_persistent(const KJob *d_jobs, const uint64_t *d_item_start, uint32_t n_jobs,
+// one persistent launch over jobs of degree D (all of d_jobs[0..n_jobs) have degree D)
+int launch_persistent(int D, const KJob *d_jobs, const uint64_t *d_item_start, uint32_t n_jobs,
                       uint64_t n_items, unsigned long long *d_counter, uint32_t max_smem,
                       const LaunchShape &sh, cudaStream_t s);
 int launch_compact(const KJob *d_jobs, uint32_t n_jobs, cudaStream_t s);
 // raise the dynamic shared memory limit of the count kernels (once per device)
 int prepare_count_kernels(void);
-int max_ctas_per_sm(int block, uint32_t smem_bytes, bool persistent, int *out);
+int max_ctas_per_sm(int D, int block, uint32_t smem_bytes, bool persistent, int *out);
 int device_sm_count(void);
 uint32_t device_smem_optin(void);
 
@@ -114,6 +129,8 @@ uint32_t device_smem_optin(void);
 void layout_job_smem(KJob &j, uint32_t smem_limit);
 // validates a job and fills a KJob (tables, layout); outputs left null
 int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n);
+// launch shape for degree D at this much dynamic smem
+int choose_shape(int D, uint32_t smem, bool persistent, LaunchShape *out);
 // hash slots for a job of `count` members (power of two)
 uint32_t hash_capacity(uint32_t g, uint32_t q, uint64_t count, uint32_t scale);
 

@@ -46,8 +46,10 @@ extern "C" int hwc_probe_smem_gather(uint32_t entries, uint32_t iters, double *r
     if (!reads_per_s || entries < 32 || entries > 100000 || iters == 0)
         return set_error(HWC_ERR_ARG, "bad probe arguments");
     const uint32_t smem = ((entries * 2 + 15) / 16) * 16;
+    cudaFuncAttributes fa{};
+    HWC_CUDA_TRY(cudaFuncGetAttributes(&fa, (const void *)k_gather));
     HWC_CUDA_TRY(cudaFuncSetAttribute((const void *)k_gather, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)device_smem_optin()));
+                                      (int)device_smem_optin() - (int)fa.sharedSizeBytes));
     int ctas = 0;
     HWC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, (const void *)k_gather, 256, smem));
     if (ctas <= 0) return set_error(HWC_ERR_TOO_LARGE, "probe table does not fit");

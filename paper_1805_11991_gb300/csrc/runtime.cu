@@ -93,30 +93,33 @@ static int validate_job(const hwc_job_t &j, uint64_t *fam_n)
 
 void layout_job_smem(KJob &j, uint32_t smem_limit)
 {
-    // try to place every k; drop the largest tables to global until it fits
-    bool in_smem[kMaxG] = {};
-    for (uint32_t k = 0; k < j.g; ++k) in_smem[k] = j.zech2[k] != nullptr;
+    // start from the cheapest layout per field (tripled, in smem) and move the
+    // largest tables to cheaper-in-space layouts until everything fits
+    uint32_t kind[kMaxG];
+    for (uint32_t k = 0; k < j.g; ++k)
+        kind[k] = j.zech3[k] ? kTabTripleSmem : (j.zech2[k] ? kTabDoubleSmem : kTabDoubleGlobal);
+    auto words = [&](uint32_t k) -> uint64_t {
+        if (kind[k] == kTabTripleSmem) return ((3ull * j.L[k] + 1 + 7) / 8) * 8;
+        if (kind[k] == kTabDoubleSmem) return ((2ull * j.L[k] + 1 + 7) / 8) * 8;
+        return 0;
+    };
     auto bytes_for = [&](void) {
         uint64_t u16 = 0;
-        for (uint32_t k = 0; k < j.g; ++k)
-            if (in_smem[k]) u16 += ((2ull * j.L[k] + 1 + 7) / 8) * 8;
+        for (uint32_t k = 0; k < j.g; ++k) u16 += words(k);
         return u16 * 2 + 4ull * j.g * ((j.q + 3) / 4) * 4;
     };
     while (bytes_for() > smem_limit) {
         int big = -1;
         for (uint32_t k = 0; k < j.g; ++k)
-            if (in_smem[k] && (big < 0 || j.L[k] > j.L[big])) big = (int)k;
+            if (kind[k] != kTabDoubleGlobal && (big < 0 || words(k) > words(big))) big = (int)k;
         if (big < 0) break;
-        in_smem[big] = false;
+        kind[big] = (kind[big] == kTabTripleSmem && j.zech2[big]) ? kTabDoubleSmem : kTabDoubleGlobal;
     }
     uint32_t off = 0;
     for (uint32_t k = 0; k < kMaxG; ++k) {
-        if (k < j.g && in_smem[k]) {
-            j.tab_off[k] = off;
-            off += ((2 * j.L[k] + 1 + 7) / 8) * 8;
-        } else {
-            j.tab_off[k] = kWideTable;
-        }
+        j.tab_kind[k] = k < j.g ? kind[k] : kTabDoubleGlobal;
+        j.tab_off[k] = off;
+        if (k < j.g) off += (uint32_t)words(k);
     }
     j.smem_u16 = off;
     uint32_t off32 = off / 2;
@@ -179,6 +182,7 @@ int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n)
         kj.L[k - 1] = t->L;
         kj.barrett[k - 1] = (uint32_t)((1ull << 32) / t->L);
         kj.zech2[k - 1] = t->d_zech2;
+        kj.zech3[k - 1] = t->d_zech3;
         kj.zech2w[k - 1] = t->d_zech2w;
         kj.coef_log[k - 1] = t->d_coef_log;
     }
@@ -248,18 +252,29 @@ hwc_hist *hwc::hist_from_keys(const KJob &kj, const unsigned long long *keys,
 // ---------------------------------------------------------------------
 // batches
 
+// Jobs of one degree share a persistent launch (the kernel is specialised on
+// the degree); a batch holds one group per distinct degree.
+struct BatchGroup {
+    int D = 0;
+    uint32_t first = 0, n = 0;       // jobs[first .. first+n) (sorted by degree)
+    uint32_t start_off = 0;          // offset of this group's item table
+    uint64_t n_items = 0;
+    uint32_t max_smem = 0;
+    LaunchShape shape;
+};
+
 struct hwc_batch {
-    std::vector<HostJob> jobs;
+    std::vector<HostJob> jobs;       // sorted by degree
+    std::vector<size_t> pos;         // caller's index -> position in jobs
+    std::vector<BatchGroup> groups;
     KJob *h_jobs = nullptr;          // pinned copy of the descriptors
     uint64_t *h_item_start = nullptr;
+    size_t n_starts = 0;
     KJob *d_jobs = nullptr;
     uint64_t *d_item_start = nullptr;
-    uint64_t n_items = 0;
-    unsigned long long *d_counter = nullptr;
+    unsigned long long *d_counters = nullptr;
     std::vector<void *> allocs;
     uint32_t flags = 0;
-    LaunchShape shape;
-    uint32_t max_smem = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     cudaEvent_t done = nullptr;
@@ -298,52 +313,57 @@ static int dalloc(hwc_batch *b, T **p, uint64_t n)
     return HWC_OK;
 }
 
-static int batch_enqueue(hwc_batch *b, cudaStream_t s)
+static int batch_enqueue(hwc_batch *b, cudaStream_t s, bool capturing)
 {
     const uint32_t nj = (uint32_t)b->jobs.size();
-    // the step's inputs: job descriptors and the work-item table, from pinned memory
+    // the step's inputs: job descriptors and the work-item tables, from pinned memory
     HWC_CUDA_TRY(cudaMemcpyAsync(b->d_jobs, b->h_jobs, nj * sizeof(KJob), cudaMemcpyHostToDevice, s));
-    HWC_CUDA_TRY(cudaMemcpyAsync(b->d_item_start, b->h_item_start, (nj + 1) * sizeof(uint64_t),
+    HWC_CUDA_TRY(cudaMemcpyAsync(b->d_item_start, b->h_item_start, b->n_starts * sizeof(uint64_t),
                                  cudaMemcpyHostToDevice, s));
-    int rc = launch_clear(b->d_jobs, nj, b->d_counter, s);
+    int rc = launch_clear(b->d_jobs, nj, b->d_counters, (uint32_t)b->groups.size(), s);
     if (rc) return rc;
-    if (b->t0) HWC_CUDA_TRY(cudaEventRecordWithFlags(b->t0, s, cudaEventRecordExternal));
+    // inside a graph capture an event record must be an external node to time anything
+    if (b->t0) HWC_CUDA_TRY(capturing ? cudaEventRecordWithFlags(b->t0, s, cudaEventRecordExternal)
+                                      : cudaEventRecord(b->t0, s));
     if (b->flags & HWC_FLAG_PLAIN) {
-        for (uint32_t i = 0; i < nj; ++i) {
-            rc = launch_plain(b->d_jobs + i, b->jobs[i].kj, b->shape, s);
+        for (const BatchGroup &G : b->groups)
+            for (uint32_t i = G.first; i < G.first + G.n; ++i) {
+                rc = launch_plain(b->d_jobs + i, b->jobs[i].kj, G.shape, s);
+                if (rc) return rc;
+            }
+    } else {
+        for (size_t g = 0; g < b->groups.size(); ++g) {
+            const BatchGroup &G = b->groups[g];
+            rc = launch_persistent(G.D, b->d_jobs + G.first, b->d_item_start + G.start_off, G.n,
+                                   G.n_items, b->d_counters + g, G.max_smem, G.shape, s);
             if (rc) return rc;
         }
-    } else {
-        rc = launch_persistent(b->d_jobs, b->d_item_start, nj, b->n_items, b->d_counter,
-                               b->max_smem, b->shape, s);
-        if (rc) return rc;
     }
-    if (b->t1) HWC_CUDA_TRY(cudaEventRecordWithFlags(b->t1, s, cudaEventRecordExternal));
+    if (b->t1) HWC_CUDA_TRY(capturing ? cudaEventRecordWithFlags(b->t1, s, cudaEventRecordExternal)
+                                      : cudaEventRecord(b->t1, s));
     return launch_compact(b->d_jobs, nj, s);
 }
 
-// pick threads per CTA to maximise resident warps per SM for this smem size
-static int choose_shape(hwc_batch *b)
+// threads per CTA that maximise resident warps per SM for this degree and smem
+int hwc::choose_shape(int D, uint32_t smem, bool persistent, LaunchShape *out)
 {
-    const bool persistent = !(b->flags & HWC_FLAG_PLAIN);
     const int sms = device_sm_count();
     int best_block = 256, best_warps = -1, best_ctas = 1;
-    for (int block : {1024, 512, 256}) {
+    for (int block : {256, 128}) {
         int ctas = 0;
-        int rc = max_ctas_per_sm(block, b->max_smem, persistent, &ctas);
+        int rc = max_ctas_per_sm(D, block, smem, persistent, &ctas);
         if (rc) return rc;
-        int warps = ctas * block / 32;
+        const int warps = ctas * block / 32;
         if (warps > best_warps) {
             best_warps = warps;
             best_block = block;
             best_ctas = ctas;
         }
     }
-    if (best_warps <= 0)
-        return set_error(HWC_ERR_TOO_LARGE, "no CTA fits %u bytes of shared memory", b->max_smem);
-    b->shape.block = best_block;
-    b->shape.grid = sms * best_ctas;
-    b->shape.item_tiles = (best_block / 32) * 2;
+    if (best_warps <= 0) return set_error(HWC_ERR_TOO_LARGE, "no CTA fits %u bytes of shared memory", smem);
+    out->block = best_block;
+    out->grid = sms * best_ctas;
+    out->item_tiles = (best_block / 32) * 2;
     return HWC_OK;
 }
 
@@ -362,9 +382,17 @@ static int batch_create_impl(const hwc_job_t *jobs, size_t n, uint32_t flags, ui
     hwc_batch *b = new hwc_batch();
     b->flags = flags;
     cudaGetDevice(&b->device);
+    // order jobs by degree (stable), remember where each caller's job went
+    std::vector<size_t> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t x, size_t y) { return jobs[x].family.degree < jobs[y].family.degree; });
+    b->pos.resize(n);
     b->jobs.resize(n);
-    for (size_t i = 0; i < n; ++i) {
-        HostJob &hj = b->jobs[i];
+    for (size_t r = 0; r < n; ++r) {
+        const size_t i = order[r];
+        b->pos[i] = r;
+        HostJob &hj = b->jobs[r];
         hj.job = jobs[i];
         rc = fill_kjob(jobs[i], hj.kj, &hj.fam_n);
         if (rc) { batch_release(b); return rc; }
@@ -377,26 +405,43 @@ static int batch_create_impl(const hwc_job_t *jobs, size_t n, uint32_t flags, ui
             batch_release(b);
             return rc;
         }
-        b->max_smem = std::max(b->max_smem, kj.smem_bytes);
+        if (b->groups.empty() || b->groups.back().D != (int)kj.d) {
+            BatchGroup G;
+            G.D = (int)kj.d;
+            G.first = (uint32_t)r;
+            b->groups.push_back(G);
+        }
+        BatchGroup &G = b->groups.back();
+        G.n++;
+        G.max_smem = std::max(G.max_smem, kj.smem_bytes);
     }
-    if ((rc = choose_shape(b))) { batch_release(b); return rc; }
-    // work items: each job is cut into items of item_tiles tiles, in job order
-    std::vector<uint64_t> starts(n + 1, 0);
-    for (size_t i = 0; i < n; ++i)
-        starts[i + 1] = starts[i] + (b->jobs[i].kj.n_tiles + b->shape.item_tiles - 1) / b->shape.item_tiles;
-    b->n_items = starts[n];
-    if ((rc = dalloc(b, &b->d_jobs, n)) || (rc = dalloc(b, &b->d_item_start, n + 1)) ||
-        (rc = dalloc(b, &b->d_counter, 1))) {
+    const bool persistent = !(flags & HWC_FLAG_PLAIN);
+    std::vector<uint64_t> starts;
+    for (BatchGroup &G : b->groups) {
+        if ((rc = choose_shape(G.D, G.max_smem, persistent, &G.shape))) { batch_release(b); return rc; }
+        // work items: each job is cut into items of item_tiles tiles, in job order
+        G.start_off = (uint32_t)starts.size();
+        uint64_t acc = 0;
+        for (uint32_t r = G.first; r < G.first + G.n; ++r) {
+            starts.push_back(acc);
+            acc += (b->jobs[r].kj.n_tiles + G.shape.item_tiles - 1) / G.shape.item_tiles;
+        }
+        starts.push_back(acc);
+        G.n_items = acc;
+    }
+    b->n_starts = starts.size();
+    if ((rc = dalloc(b, &b->d_jobs, n)) || (rc = dalloc(b, &b->d_item_start, b->n_starts)) ||
+        (rc = dalloc(b, &b->d_counters, b->groups.size()))) {
         batch_release(b);
         return rc;
     }
     if (cudaMallocHost(&b->h_jobs, n * sizeof(KJob)) != cudaSuccess ||
-        cudaMallocHost(&b->h_item_start, (n + 1) * sizeof(uint64_t)) != cudaSuccess) {
+        cudaMallocHost(&b->h_item_start, b->n_starts * sizeof(uint64_t)) != cudaSuccess) {
         cudaGetLastError();
         batch_release(b);
         return set_error(HWC_ERR_NOMEM, "pinned host allocation failed");
     }
-    for (size_t i = 0; i < n; ++i) b->h_jobs[i] = b->jobs[i].kj;
+    for (size_t r = 0; r < n; ++r) b->h_jobs[r] = b->jobs[r].kj;
     std::copy(starts.begin(), starts.end(), b->h_item_start);
     if (flags & HWC_FLAG_TIMING) {
         if (cudaEventCreate(&b->t0) != cudaSuccess || cudaEventCreate(&b->t1) != cudaSuccess) {
@@ -404,7 +449,7 @@ static int batch_create_impl(const hwc_job_t *jobs, size_t n, uint32_t flags, ui
             return set_error(HWC_ERR_CUDA, "cudaEventCreate failed");
         }
     }
-    b->launches_per_run = 2 + ((flags & HWC_FLAG_PLAIN) ? (uint32_t)n : 1u);
+    b->launches_per_run = 2 + (uint32_t)(persistent ? b->groups.size() : n);
     if (cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess) {
         batch_release(b);
         return set_error(HWC_ERR_CUDA, "cudaEventCreate failed");
@@ -417,7 +462,7 @@ static int batch_create_impl(const hwc_job_t *jobs, size_t n, uint32_t flags, ui
         }
         cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (ce == cudaSuccess) {
-            rc = batch_enqueue(b, cs);
+            rc = batch_enqueue(b, cs, true);
             cudaError_t ce2 = cudaStreamEndCapture(cs, &b->graph);
             if (rc == HWC_OK && ce2 == cudaSuccess)
                 ce = cudaGraphInstantiate(&b->gexec, b->graph, 0);
@@ -440,7 +485,7 @@ static int batch_result_impl(hwc_batch *b, size_t i, hwc_hist **out)
     if (!b->launched) return set_error(HWC_ERR_STATE, "batch was not launched");
     if (i >= b->jobs.size()) return set_error(HWC_ERR_ARG, "job %zu out of range", i);
     HWC_CUDA_TRY(cudaEventSynchronize(b->done));
-    const KJob &kj = b->jobs[i].kj;
+    const KJob &kj = b->jobs[b->pos[i]].kj;
     unsigned long long st[3] = {}, n_out = 0;
     HWC_CUDA_TRY(cudaMemcpy(st, kj.stats, sizeof st, cudaMemcpyDeviceToHost));
     HWC_CUDA_TRY(cudaMemcpy(&n_out, kj.n_out, sizeof n_out, cudaMemcpyDeviceToHost));
@@ -476,7 +521,7 @@ extern "C" int hwc_batch_launch(hwc_batch_t *b, void *stream)
     if (b->gexec) {
         HWC_CUDA_TRY(cudaGraphLaunch(b->gexec, s));
     } else {
-        int rc = batch_enqueue(b, s);
+        int rc = batch_enqueue(b, s, false);
         if (rc) return rc;
     }
     HWC_CUDA_TRY(cudaEventRecord(b->done, s));
@@ -500,7 +545,7 @@ extern "C" int hwc_batch_kernel_launches(const hwc_batch_t *b, uint32_t *n)
 extern "C" int hwc_batch_io_bytes(const hwc_batch_t *b, uint64_t *h2d, uint64_t *d2h)
 {
     if (!b) return set_error(HWC_ERR_ARG, "batch is NULL");
-    if (h2d) *h2d = b->jobs.size() * sizeof(KJob) + (b->jobs.size() + 1) * sizeof(uint64_t);
+    if (h2d) *h2d = b->jobs.size() * sizeof(KJob) + b->n_starts * sizeof(uint64_t);
     if (d2h) *d2h = b->d2h_last;
     return HWC_OK;
 }
@@ -601,14 +646,8 @@ extern "C" int hwc_count_members(uint32_t g, uint32_t q, const hwc_family_t *fam
         return set_error(HWC_ERR_CUDA, "setup: %s", cudaGetErrorString(ce));
     }
     LaunchShape sh;
-    sh.block = 256;
-    int ctas = 0;
-    rc = max_ctas_per_sm(sh.block, kj.smem_bytes, false, &ctas);
-    if (rc == HWC_OK && ctas <= 0) rc = set_error(HWC_ERR_TOO_LARGE, "no CTA fits");
-    if (rc == HWC_OK) {
-        sh.grid = device_sm_count() * ctas;
-        rc = launch_plain(b->d_jobs, kj, sh, s);
-    }
+    rc = choose_shape((int)kj.d, kj.smem_bytes, false, &sh);
+    if (rc == HWC_OK) rc = launch_plain(b->d_jobs, kj, sh, s);
     if (rc == HWC_OK) {
         ce = cudaMemcpyAsync(counts, kj.member_counts, count * g * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
         if (ce == cudaSuccess) ce = cudaMemcpyAsync(sqf, kj.member_sqf, count, cudaMemcpyDeviceToHost, s);

@@ -11,6 +11,7 @@
 // depend on how requests were mixed: every slice adds exact integer counts.
 #include "hwc_internal.cuh"
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -56,11 +57,11 @@ struct hwc_server {
     uint64_t used_bytes = 0;
     std::set<std::pair<uint32_t, uint32_t>> tables_seen;
     KJob *d_jobs = nullptr;
-    uint64_t *d_item_start = nullptr;
-    unsigned long long *d_counter = nullptr;
+    uint64_t *d_item_start = nullptr;     // [2 * max_active]
+    unsigned long long *d_counters = nullptr;   // [max_active]
     KJob *h_jobs = nullptr;          // pinned staging
     uint64_t *h_item_start = nullptr;
-    std::map<uint32_t, LaunchShape> shapes;
+    std::map<std::pair<int, uint32_t>, LaunchShape> shapes;
     uint64_t steps = 0;
 };
 
@@ -85,29 +86,17 @@ int ralloc(Request *r, T **p, uint64_t n)
     return HWC_OK;
 }
 
-int shape_for(hwc_server *s, uint32_t smem, LaunchShape *out)
+int shape_for(hwc_server *s, int D, uint32_t smem, LaunchShape *out)
 {
-    auto it = s->shapes.find(smem);
+    auto key = std::make_pair(D, smem);
+    auto it = s->shapes.find(key);
     if (it != s->shapes.end()) {
         *out = it->second;
         return HWC_OK;
     }
-    LaunchShape best;
-    int best_warps = -1;
-    for (int block : {1024, 512, 256}) {
-        int ctas = 0;
-        int rc = max_ctas_per_sm(block, smem, true, &ctas);
-        if (rc) return rc;
-        if (ctas * block / 32 > best_warps) {
-            best_warps = ctas * block / 32;
-            best.block = block;
-            best.grid = ctas * device_sm_count();
-        }
-    }
-    if (best_warps <= 0) return set_error(HWC_ERR_TOO_LARGE, "no CTA fits %u bytes", smem);
-    best.item_tiles = best.block / 32;
-    s->shapes[smem] = best;
-    *out = best;
+    int rc = choose_shape(D, smem, true, out);
+    if (rc) return rc;
+    s->shapes[key] = *out;
     return HWC_OK;
 }
 
@@ -124,7 +113,7 @@ int admit(hwc_server *s, Request *r)
     KJob *d_one = nullptr;
     if ((rc = ralloc(r, &d_one, 1))) return rc;
     HWC_CUDA_TRY(cudaMemcpyAsync(d_one, &kj, sizeof kj, cudaMemcpyHostToDevice, s->stream));
-    rc = launch_clear(d_one, 1, nullptr, s->stream);
+    rc = launch_clear(d_one, 1, nullptr, 0, s->stream);
     if (rc) return rc;
     HWC_CUDA_TRY(cudaStreamSynchronize(s->stream));
     return HWC_OK;
@@ -203,42 +192,68 @@ void server_loop(hwc_server *s)
             step = s->active;
         }
 
-        // one device step: a fair share of tiles of every active request
+        // one device step: a fair share of tiles of every active request; requests
+        // of one degree share a persistent launch
+        std::stable_sort(step.begin(), step.end(),
+                         [](const Request *x, const Request *y) { return x->kj.d < y->kj.d; });
         const uint32_t n = (uint32_t)step.size();
-        uint32_t smem = 0;
-        for (Request *r : step) smem = std::max(smem, r->kj.smem_bytes);
-        LaunchShape sh;
-        int rc = shape_for(s, smem, &sh);
-        uint64_t budget = s->cfg.step_items ? s->cfg.step_items : (uint64_t)sh.grid * 4;
-        budget *= (uint64_t)sh.item_tiles;
-        const uint64_t share = std::max<uint64_t>(sh.item_tiles, budget / n);
-        std::vector<uint64_t> took(n);
-        uint64_t items = 0;
-        for (uint32_t i = 0; i < n; ++i) {
-            Request *r = step[i];
-            KJob sl = r->kj;
-            const uint64_t left = r->kj.n_tiles - r->next_tile;
-            const uint64_t t = std::min(left, share);
-            took[i] = t;
-            sl.first = r->kj.first + r->next_tile * kTileMembers;
-            sl.count = std::min<uint64_t>(r->kj.count - r->next_tile * kTileMembers, t * kTileMembers);
-            sl.n_tiles = t;
-            s->h_jobs[i] = sl;
-            s->h_item_start[i] = items;
-            items += (t + sh.item_tiles - 1) / sh.item_tiles;
+        std::vector<uint64_t> took(n, 0);
+        int rc = HWC_OK;
+        uint32_t item_off = 0, ngroups = 0;
+        struct StepGroup {
+            int D;
+            uint32_t first, n, off;
+            uint64_t items;
+            uint32_t smem;
+            LaunchShape sh;
+        };
+        std::vector<StepGroup> groups;
+        for (uint32_t i = 0; i < n && rc == HWC_OK;) {
+            uint32_t e = i;
+            uint32_t smem = 0;
+            while (e < n && step[e]->kj.d == step[i]->kj.d) smem = std::max(smem, step[e++]->kj.smem_bytes);
+            StepGroup G{(int)step[i]->kj.d, i, e - i, item_off, 0, smem, LaunchShape()};
+            rc = shape_for(s, G.D, smem, &G.sh);
+            if (rc) break;
+            uint64_t budget = s->cfg.step_items ? s->cfg.step_items : (uint64_t)G.sh.grid * 4;
+            budget *= (uint64_t)G.sh.item_tiles;
+            const uint64_t share = std::max<uint64_t>(G.sh.item_tiles, budget / n);
+            uint64_t items = 0;
+            for (uint32_t r = i; r < e; ++r) {
+                Request *q = step[r];
+                KJob sl = q->kj;
+                const uint64_t left = q->kj.n_tiles - q->next_tile;
+                const uint64_t t = std::min(left, share);
+                took[r] = t;
+                sl.first = q->kj.first + q->next_tile * kTileMembers;
+                sl.count = std::min<uint64_t>(q->kj.count - q->next_tile * kTileMembers, t * kTileMembers);
+                sl.n_tiles = t;
+                s->h_jobs[r] = sl;
+                s->h_item_start[item_off + (r - i)] = items;
+                items += (t + G.sh.item_tiles - 1) / G.sh.item_tiles;
+            }
+            s->h_item_start[item_off + (e - i)] = items;
+            G.items = items;
+            item_off += (e - i) + 1;
+            groups.push_back(G);
+            ++ngroups;
+            i = e;
         }
-        s->h_item_start[n] = items;
         cudaError_t ce = cudaSuccess;
         if (rc == HWC_OK) {
             ce = cudaMemcpyAsync(s->d_jobs, s->h_jobs, n * sizeof(KJob), cudaMemcpyHostToDevice, s->stream);
             if (ce == cudaSuccess)
-                ce = cudaMemcpyAsync(s->d_item_start, s->h_item_start, (n + 1) * sizeof(uint64_t),
+                ce = cudaMemcpyAsync(s->d_item_start, s->h_item_start, item_off * sizeof(uint64_t),
                                      cudaMemcpyHostToDevice, s->stream);
-            if (ce == cudaSuccess) ce = cudaMemsetAsync(s->d_counter, 0, sizeof(unsigned long long), s->stream);
+            if (ce == cudaSuccess)
+                ce = cudaMemsetAsync(s->d_counters, 0, ngroups * sizeof(unsigned long long), s->stream);
             if (ce != cudaSuccess) rc = set_error(HWC_ERR_CUDA, "step setup: %s", cudaGetErrorString(ce));
         }
-        if (rc == HWC_OK)
-            rc = launch_persistent(s->d_jobs, s->d_item_start, n, items, s->d_counter, smem, sh, s->stream);
+        for (size_t g = 0; rc == HWC_OK && g < groups.size(); ++g) {
+            const StepGroup &G = groups[g];
+            rc = launch_persistent(G.D, s->d_jobs + G.first, s->d_item_start + G.off, G.n, G.items,
+                                   s->d_counters + g, G.smem, G.sh, s->stream);
+        }
         if (rc == HWC_OK) {
             ce = cudaStreamSynchronize(s->stream);
             if (ce != cudaSuccess) rc = set_error(HWC_ERR_CUDA, "step: %s", cudaGetErrorString(ce));
@@ -281,10 +296,10 @@ extern "C" int hwc_serve_open(const hwc_server_config_t *cfg, hwc_server_t **out
     const uint32_t m = s->cfg.max_active;
     bool ok = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) == cudaSuccess &&
               cudaMalloc(&s->d_jobs, m * sizeof(KJob)) == cudaSuccess &&
-              cudaMalloc(&s->d_item_start, (m + 1) * sizeof(uint64_t)) == cudaSuccess &&
-              cudaMalloc(&s->d_counter, sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMalloc(&s->d_item_start, 2 * (m + 1) * sizeof(uint64_t)) == cudaSuccess &&
+              cudaMalloc(&s->d_counters, m * sizeof(unsigned long long)) == cudaSuccess &&
               cudaMallocHost(&s->h_jobs, m * sizeof(KJob)) == cudaSuccess &&
-              cudaMallocHost(&s->h_item_start, (m + 1) * sizeof(uint64_t)) == cudaSuccess;
+              cudaMallocHost(&s->h_item_start, 2 * (m + 1) * sizeof(uint64_t)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         hwc_serve_close(s);
@@ -374,7 +389,7 @@ extern "C" int hwc_serve_close(hwc_server_t *s)
     }
     cudaFree(s->d_jobs);
     cudaFree(s->d_item_start);
-    cudaFree(s->d_counter);
+    cudaFree(s->d_counters);
     if (s->h_jobs) cudaFreeHost(s->h_jobs);
     if (s->h_item_start) cudaFreeHost(s->h_item_start);
     if (s->stream) cudaStreamDestroy(s->stream);

@@ -252,27 +252,30 @@ __global__ void k_antilog(ModPoly m, uint32_t L, uint32_t B, uint32_t *antilog, 
     }
 }
 
-// Z[u] = log(1 + alpha^u) (L if zero); kernel layouts doubled over [0, 2L]
+// Z[u] = log(1 + alpha^u) (L if zero), and the layouts the count kernels read:
+// doubled over [0, 2L] with poison 2L, tripled over [0, 3L] with poison 3L.
 __global__ void k_zech(uint32_t p, uint32_t L, const uint32_t *__restrict__ antilog,
                        const uint32_t *__restrict__ logt, uint32_t *zech, uint16_t *zech2,
-                       uint32_t *zech2w)
+                       uint32_t *zech2w, uint16_t *zech3)
 {
-    for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u <= 2ull * L;
+    const uint64_t top = zech3 ? 3ull * L : 2ull * L;
+    for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u <= top;
          u += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t z2;
-        if (u == 2ull * L) {
-            z2 = 2 * L;
-        } else {
-            uint32_t um = (uint32_t)(u < L ? u : u - L);
-            uint32_t v = antilog[um];
-            uint32_t d0 = v % p;
-            uint32_t w = v - d0 + (d0 + 1 == p ? 0 : d0 + 1);   // v + 1
-            uint32_t z = (w == 0) ? L : logt[w];
-            if (u < L) zech[u] = z;
-            z2 = (z == L) ? 2 * L : z;
+        uint32_t z = L;
+        if (u < 3ull * L) {
+            const uint32_t um = (uint32_t)(u % L);
+            const uint32_t v = antilog[um];
+            const uint32_t d0 = v % p;
+            const uint32_t w = v - d0 + (d0 + 1 == p ? 0 : d0 + 1);   // v + 1
+            z = (w == 0) ? L : logt[w];
         }
-        zech2w[u] = z2;
-        if (zech2) zech2[u] = (uint16_t)z2;
+        if (u < L) zech[u] = z;
+        if (u <= 2ull * L) {
+            const uint32_t z2 = (u == 2ull * L || z == L) ? 2 * L : z;
+            zech2w[u] = z2;
+            if (zech2) zech2[u] = (uint16_t)z2;
+        }
+        if (zech3) zech3[u] = (uint16_t)((u == 3ull * L || z == L) ? 3 * L : z);
     }
 }
 
@@ -341,6 +344,7 @@ void tables_destroy(Tables *t)
     cudaFree(t->d_coef_log);
     cudaFree(t->d_zech2);
     cudaFree(t->d_zech2w);
+    cudaFree(t->d_zech3);
     if (t->device >= 0 && t->device != cur && cur >= 0) cudaSetDevice(cur);
     delete t;
 }
@@ -409,6 +413,8 @@ int tables_build(uint32_t q, uint32_t k, Tables **out)
               cudaMalloc(&t->d_zech2w, sizeof(uint32_t) * (2ull * L + 1)) == cudaSuccess;
     if (ok && 2ull * L < 65536ull)
         ok = cudaMalloc(&t->d_zech2, sizeof(uint16_t) * (2ull * L + 1)) == cudaSuccess;
+    if (ok && 3ull * L < 65536ull)
+        ok = cudaMalloc(&t->d_zech3, sizeof(uint16_t) * (3ull * L + 1)) == cudaSuccess;
     if (!ok) {
         cudaFree(d_best);
         return fail(set_error(HWC_ERR_NOMEM, "cudaMalloc of tables for Q=%u failed", t->Q));
@@ -421,8 +427,8 @@ int tables_build(uint32_t q, uint32_t k, Tables **out)
     const uint32_t B = 64;
     uint64_t nthr = (L + B - 1) / B;
     k_antilog<<<(unsigned)((nthr + 127) / 128), 128>>>(mp, L, B, t->d_antilog, t->d_log);
-    k_zech<<<std::max(1u, std::min(4096u, (unsigned)((2ull * L + 256) / 256))), 256>>>(
-        p, L, t->d_antilog, t->d_log, t->d_zech, t->d_zech2, t->d_zech2w);
+    k_zech<<<std::max(1u, std::min(4096u, (unsigned)((3ull * L + 256) / 256))), 256>>>(
+        p, L, t->d_antilog, t->d_log, t->d_zech, t->d_zech2, t->d_zech2w, t->d_zech3);
 
     // 3. logs of the F_q digits
     ElemArgs ea{};

@@ -78,8 +78,14 @@ def config5():
     return jobs
 
 
+def config2_q31d5():
+    """One job of config 2 (q=31, degree 5, 31^4 members): the small case used
+    for detailed profiles of the count kernel."""
+    return [JobSpec(2, 31, MONIC_NOSUB, 5)]
+
+
 CONFIGS = {"config1": config1, "config2": config2, "config3": config3, "config4": config4,
-           "config5": config5}
+           "config5": config5, "config2_q31d5": config2_q31d5}
 
 
 def poisson_arrivals(n: int, rate_per_s: float, seed: int = 11) -> np.ndarray:
