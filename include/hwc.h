@@ -143,10 +143,11 @@ int hwc_count(uint32_t g, uint32_t q, const hwc_family_t *fam, uint64_t first,
 /* Per-member counts (for checking): counts[i*g + k-1] = #C(F_{q^k}) and
  * sqf[i] = 1 if member first+i is square-free.  With unfiltered = 0 the
  * counts of non-square-free members are 0; with unfiltered = 1 they are the
- * point-count formula applied anyway.  `counts` (count*g int32) and `sqf`
- * (count bytes) are HOST arrays.  Synchronous. */
+ * point-count formula applied anyway.  flags: 0 or HWC_FLAG_HORNER (use the
+ * per-member kernel even where the c_0 fan-out kernel applies).  `counts`
+ * (count*g int32) and `sqf` (count bytes) are HOST arrays.  Synchronous. */
 int hwc_count_members(uint32_t g, uint32_t q, const hwc_family_t *fam,
-                      uint64_t first, uint64_t count, int unfiltered,
+                      uint64_t first, uint64_t count, int unfiltered, uint32_t flags,
                       void *stream, int32_t *counts, uint8_t *sqf);
 
 /* Histogram contents.  n_entries distinct tuples; n_squarefree = sum of the

@@ -1,0 +1,245 @@
+// count_common.cuh -- device pieces shared by the count kernels: table
+// access, member decoding, the square-free test, Zech chain steps and the
+// histogram hash.  Included by count_kernels.cu and fanout_kernels.cu only.
+#pragma once
+#include "hwc_internal.cuh"
+
+namespace hwc {
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+struct TabS {   // u16 table in shared memory
+    const uint16_t *t;
+    __device__ __forceinline__ uint32_t operator[](uint32_t u) const { return t[u]; }
+};
+struct TabG {   // u32 table in global memory (L1/L2 resident)
+    const uint32_t *t;
+    __device__ __forceinline__ uint32_t operator[](uint32_t u) const { return __ldg(t + u); }
+};
+
+__device__ __forceinline__ uint32_t addmod(uint32_t a, uint32_t b, uint32_t L)
+{
+    uint32_t s = a + b;
+    return s >= L ? s - L : s;
+}
+
+// (g * j) mod L for g * j < 2^32, Barrett with bar = floor(2^32 / L)
+__device__ __forceinline__ uint32_t mulmod_small(uint32_t g, uint32_t j, uint32_t L, uint32_t bar)
+{
+    uint32_t t = g * j;
+    uint32_t qt = __umulhi(t, bar);
+    uint32_t r = t - qt * L;
+    return r >= L ? r - L : r;
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// SplitMix64 output for state seed + (j+1)*gamma (Steele, Lea, Flood 2014)
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t j)
+{
+    return mix64(seed + (j + 1) * 0x9E3779B97F4A7C15ull);
+}
+
+// ---------------------------------------------------------------------
+// member decoding (Algorithm 1 line 3; family definitions in hwc.h)
+
+template <int D>
+__device__ __forceinline__ void decode_member(const KJob &J, uint64_t m, uint32_t (&c)[D + 1])
+{
+    uint64_t idx = J.first + m;
+    uint32_t kind = J.kind;
+    if (kind == HWC_FAM_MONIC_NOSUB_SAMPLED) {
+        idx = __umul64hi(splitmix64_at(J.seed, idx), J.fam_mz);
+        kind = HWC_FAM_MONIC_NOSUB;
+    }
+    const uint32_t q = J.q;
+    const int ndig = (kind == HWC_FAM_ALL_DEG) ? D : D - 1;
+    uint64_t r = idx;
+#pragma unroll
+    for (int i = 0; i <= D; ++i) {
+        if (i < ndig) {
+            if (r >> 32) {
+                c[i] = (uint32_t)(r % q);
+                r /= q;
+            } else {
+                uint32_t r32 = (uint32_t)r;
+                c[i] = r32 % q;
+                r = r32 / q;
+            }
+        }
+    }
+    if (kind == HWC_FAM_ALL_DEG) {
+        c[D] = 1 + (uint32_t)r;
+    } else {
+        c[D - 1] = 0;
+        c[D] = 1;
+    }
+}
+
+// ---------------------------------------------------------------------
+// square-freeness: gcd(f, f') in Zech arithmetic over F_q (k = 1 tables).
+// Elements as logs, zero = L1.
+
+template <class Tab>
+struct FqLog {
+    Tab T;
+    uint32_t L;
+    __device__ __forceinline__ uint32_t mul(uint32_t a, uint32_t b) const
+    {
+        return (a == L || b == L) ? L : addmod(a, b, L);
+    }
+    __device__ __forceinline__ uint32_t neg(uint32_t a) const
+    {
+        return a == L ? L : addmod(a, L >> 1, L);
+    }
+    __device__ __forceinline__ uint32_t add(uint32_t a, uint32_t b) const
+    {
+        if (a == L) return b;
+        if (b == L) return a;
+        uint32_t n = addmod(a, L - b, L);
+        uint32_t z = T[n];
+        return z >= 2 * L ? L : addmod(b, z, L);
+    }
+};
+
+template <int D, class Tab>
+__device__ bool squarefree(const FqLog<Tab> &F, const uint32_t *coef1, uint32_t p,
+                           const uint32_t (&c)[D + 1])
+{
+    const uint32_t Z = F.L;
+    uint32_t P[2][D + 1];
+    int dg[2];
+    for (int i = 0; i <= D; ++i) P[0][i] = coef1[c[i]];
+    // f' = sum i c_i x^(i-1); the integer i is the F_p digit (i mod p)
+    for (int i = 1; i <= D; ++i) P[1][i - 1] = F.mul(coef1[i % p], P[0][i]);
+    P[1][D] = Z;
+    dg[0] = D;
+    dg[1] = D - 1;
+    while (dg[0] >= 0 && P[0][dg[0]] == Z) --dg[0];
+    while (dg[1] >= 0 && P[1][dg[1]] == Z) --dg[1];
+    if (dg[1] < 0) return false;
+    int a = 0, b = 1;
+    while (dg[b] >= 0) {
+        const int db = dg[b];
+        const uint32_t il = (F.L - P[b][db]) % F.L;   // inverse of the lead
+        for (int t = dg[a]; t >= db; --t) {
+            if (P[a][t] == Z) continue;
+            const uint32_t cf = F.mul(P[a][t], il);
+            for (int i = 0; i <= db; ++i)
+                P[a][t - db + i] = F.add(P[a][t - db + i], F.neg(F.mul(cf, P[b][i])));
+        }
+        int da = db - 1;
+        while (da >= 0 && P[a][da] == Z) --da;
+        dg[a] = da;
+        int tmp = a; a = b; b = tmp;
+    }
+    return dg[a] == 0;
+}
+
+// ---------------------------------------------------------------------
+// one field: sum over x in F_Q^x of chi(f(x)) for this lane's share of x
+//
+// Two table layouts: TRIPLE (entries over [0, 3L], poison 3L) lets a step be
+// u <- min(T[u] + d + g*j, 3L) with d, g*j < L and no reduction; DOUBLE
+// (entries over [0, 2L], poison 2L) reduces d + g*j mod L first.
+
+// Horner in the log domain with explicit zero handling, for the rare x at
+// which some partial sum vanishes (the chain above then holds the poison).
+template <int D, class Tab>
+__device__ __forceinline__ int slow_chi(const Tab T, uint32_t L, uint32_t cap,
+                                        const uint32_t (&lam)[D + 1], uint32_t nz, uint32_t j)
+{
+    uint32_t l = lam[D];
+    bool zero = false;
+#pragma unroll
+    for (int i = D - 1; i >= 0; --i) {
+        if (!zero) l = addmod(l, j, L);
+        if ((nz >> i) & 1u) {
+            if (zero) {
+                l = lam[i];
+                zero = false;
+            } else {
+                const uint32_t n = addmod(l, L - lam[i], L);
+                const uint32_t z = T[n];
+                if (z >= cap) zero = true;
+                else l = addmod(lam[i], z, L);
+            }
+        }
+    }
+    return zero ? 0 : ((l & 1u) ? -1 : 1);
+}
+
+template <bool TRIPLE>
+__device__ __forceinline__ uint32_t chain_step(uint32_t z, uint32_t d, uint32_t m, uint32_t L, uint32_t cap)
+{
+    if (TRIPLE) return min(z + d + m, cap);
+    return min(z + addmod(d, m, L), cap);
+}
+
+// dense chain: every coefficient below position I1 is nonzero (all gaps 1)
+// ---------------------------------------------------------------------
+// histogram
+
+__device__ __forceinline__ void hist_insert(const KJob &J, unsigned long long key, uint32_t cnt)
+{
+    uint32_t h = (uint32_t)mix64(key) & J.hmask;
+    for (uint32_t probe = 0; probe <= J.hmask; ++probe) {
+        unsigned long long cur = *((volatile unsigned long long *)&J.hkeys[h]);
+        if (cur == kEmptyKey) cur = atomicCAS(&J.hkeys[h], kEmptyKey, key);
+        if (cur == kEmptyKey || cur == key) {
+            atomicAdd(&J.hcounts[h], (unsigned long long)cnt);
+            return;
+        }
+        h = (h + 1) & J.hmask;
+    }
+    atomicOr(&J.stats[2], 1ull);   // table full
+}
+
+struct WarpStats {
+    uint32_t examined = 0, sqf = 0;
+};
+
+// copy the job's tables into shared memory (all threads of the CTA)
+__device__ void stage_job(const KJob &J, uint8_t *smem)
+{
+    uint16_t *s16 = reinterpret_cast<uint16_t *>(smem);
+    uint32_t *s32 = reinterpret_cast<uint32_t *>(smem);
+    for (uint32_t k = 0; k < J.g; ++k) {
+        if (J.tab_kind[k] != kTabDoubleGlobal) {
+            const bool tri = J.tab_kind[k] == kTabTripleSmem;
+            const uint32_t n = (tri ? 3 : 2) * J.L[k] + 1;
+            const uint16_t *src = tri ? J.zech3[k] : J.zech2[k];
+            uint16_t *dst = s16 + J.tab_off[k];
+            for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+        }
+        const uint32_t *src = J.coef_log[k];
+        uint32_t *dst = s32 + J.coef_off[k];
+        for (uint32_t i = threadIdx.x; i < J.q; i += blockDim.x) dst[i] = src[i];
+        if (J.method == 1) {
+            const uint32_t nw = J.L[k] * J.words;
+            const uint32_t *rs = reinterpret_cast<const uint32_t *>(J.rows[k]);
+            uint32_t *rd = reinterpret_cast<uint32_t *>(smem + J.row_off[k]);
+            for (uint32_t i = threadIdx.x; i < nw; i += blockDim.x) rd[i] = rs[i];
+            uint8_t *zd = smem + J.zdig_off[k];
+            for (uint32_t i = threadIdx.x; i + 1 < J.q; i += blockDim.x) zd[i] = J.zdig[k][i];
+        }
+    }
+}
+
+__device__ __forceinline__ void flush_stats(const KJob &J, WarpStats &st, int lane)
+{
+    if (lane == 0 && (st.examined | st.sqf)) {
+        atomicAdd(&J.stats[0], (unsigned long long)st.examined);
+        atomicAdd(&J.stats[1], (unsigned long long)st.sqf);
+    }
+    st.examined = st.sqf = 0;
+}
+
+}  // namespace
+}  // namespace hwc

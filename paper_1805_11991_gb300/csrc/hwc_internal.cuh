@@ -56,6 +56,12 @@ struct Tables {
     // a step index z + d + j with z, d, j < L needs no reduction.  u16 when
     // 3L < 65536.
     uint16_t *d_zech3 = nullptr;    // [3L+1] or null
+    // Fan-out rows (q <= 63): bit c of row l is 1 iff chi(alpha^l + c) = -1 for
+    // the F_q digit c; the top bit (31 or 63) marks rows with alpha^l in F_q^x,
+    // where alpha^l + c = 0 for the digit c = zdig[l / (L/(q-1))].
+    uint32_t *d_rows32 = nullptr;   // [L] when q <= 31
+    unsigned long long *d_rows64 = nullptr;   // [L] when q <= 63
+    uint8_t *d_zdig = nullptr;      // [q-1]
 };
 
 // where a count kernel reads the Zech table of one field
@@ -93,6 +99,15 @@ struct KJob {
     const uint32_t *coef_log[kMaxG];
     uint32_t smem_u16;                // u16 words of zech2 tables staged in smem
     uint32_t smem_bytes;              // total dynamic smem for this job
+    // c_0 fan-out (method 1): groups of q members that differ only in c_0
+    uint32_t method;                  // 0 Horner tiles of 32 members, 1 fan-out groups
+    uint32_t words;                   // row words: 1 (q <= 31) or 2 (q <= 63)
+    uint64_t first_group;             // group of member `first`
+    const void *rows[kMaxG];          // d_rows32 / d_rows64
+    const uint8_t *zdig[kMaxG];
+    uint32_t row_off[kMaxG];          // byte offset of the rows in smem
+    uint32_t zdig_off[kMaxG];         // byte offset of zdig in smem
+    uint32_t zdiv[kMaxG];             // ceil(2^32 / (L/(q-1))): l / s by a high multiply
     // outputs
     unsigned long long *hkeys;        // [hmask+1]
     unsigned long long *hcounts;      // [hmask+1]
@@ -114,23 +129,27 @@ struct LaunchShape {
 int launch_clear(const KJob *d_jobs, uint32_t n_jobs, unsigned long long *d_counters,
                  uint32_t n_counters, cudaStream_t s);
 int launch_plain(const KJob *d_job, const KJob &h_job, const LaunchShape &sh, cudaStream_t s);
-// one persistent launch over jobs of degree D (all of d_jobs[0..n_jobs) have degree D)
-int launch_persistent(int D, const KJob *d_jobs, const uint64_t *d_item_start, uint32_t n_jobs,
-                      uint64_t n_items, unsigned long long *d_counter, uint32_t max_smem,
-                      const LaunchShape &sh, cudaStream_t s);
+// one persistent launch over jobs of one degree, method and row width
+int launch_persistent(int D, uint32_t method, uint32_t words, const KJob *d_jobs,
+                      const uint64_t *d_item_start, uint32_t n_jobs, uint64_t n_items,
+                      unsigned long long *d_counter, uint32_t max_smem, const LaunchShape &sh,
+                      cudaStream_t s);
 int launch_compact(const KJob *d_jobs, uint32_t n_jobs, cudaStream_t s);
 // raise the dynamic shared memory limit of the count kernels (once per device)
 int prepare_count_kernels(void);
-int max_ctas_per_sm(int D, int block, uint32_t smem_bytes, bool persistent, int *out);
+int max_ctas_per_sm(int D, uint32_t method, uint32_t words, int block, uint32_t smem_bytes,
+                    bool persistent, int *out);
 int device_sm_count(void);
 uint32_t device_smem_optin(void);
 
-// fills the job's smem layout (tab_off, coef_off, smem_bytes) given tables
-void layout_job_smem(KJob &j, uint32_t smem_limit);
-// validates a job and fills a KJob (tables, layout); outputs left null
-int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n);
-// launch shape for degree D at this much dynamic smem
-int choose_shape(int D, uint32_t smem, bool persistent, LaunchShape *out);
+// fills the job's smem layout (tab_off, coef_off, row_off, smem_bytes)
+bool layout_job_smem(KJob &j, uint32_t smem_limit);
+// validates a job and fills a KJob (tables, method, layout); outputs left null
+int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n, uint32_t flags);
+// launch shape for a kernel (degree, method, row words) at this much dynamic smem
+int choose_shape(int D, uint32_t method, uint32_t words, uint32_t smem, bool persistent, LaunchShape *out);
+// fan-out kernels (fanout_kernels.cu)
+const void *fan_kernel(int D, int W, bool persistent);
 // hash slots for a job of `count` members (power of two)
 uint32_t hash_capacity(uint32_t g, uint32_t q, uint64_t count, uint32_t scale);
 

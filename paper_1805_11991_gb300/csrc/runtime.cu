@@ -91,10 +91,13 @@ static int validate_job(const hwc_job_t &j, uint64_t *fam_n)
 // ---------------------------------------------------------------------
 // shared-memory layout of one job: u16 Zech tables first, then u32 coef logs
 
-void layout_job_smem(KJob &j, uint32_t smem_limit)
+// Shared-memory layout of one job: u16 Zech tables, u32 digit logs and, for
+// the fan-out method, the fan-out rows (4 or 8 bytes each) and zdig bytes.
+// Starts from the fastest layout per field (tripled Zech table in smem) and
+// moves the largest tables to cheaper-in-space layouts until the job fits.
+// Returns false if a fan-out job cannot keep its rows in shared memory.
+bool layout_job_smem(KJob &j, uint32_t smem_limit)
 {
-    // start from the cheapest layout per field (tripled, in smem) and move the
-    // largest tables to cheaper-in-space layouts until everything fits
     uint32_t kind[kMaxG];
     for (uint32_t k = 0; k < j.g; ++k)
         kind[k] = j.zech3[k] ? kTabTripleSmem : (j.zech2[k] ? kTabDoubleSmem : kTabDoubleGlobal);
@@ -103,10 +106,16 @@ void layout_job_smem(KJob &j, uint32_t smem_limit)
         if (kind[k] == kTabDoubleSmem) return ((2ull * j.L[k] + 1 + 7) / 8) * 8;
         return 0;
     };
+    auto fan_bytes = [&](void) -> uint64_t {
+        if (j.method != 1) return 0;
+        uint64_t b = 0;
+        for (uint32_t k = 0; k < j.g; ++k) b += 4ull * j.words * j.L[k] + ((j.q + 15) / 16) * 16;
+        return b;
+    };
     auto bytes_for = [&](void) {
         uint64_t u16 = 0;
         for (uint32_t k = 0; k < j.g; ++k) u16 += words(k);
-        return u16 * 2 + 4ull * j.g * ((j.q + 3) / 4) * 4;
+        return u16 * 2 + 4ull * j.g * ((j.q + 3) / 4) * 4 + fan_bytes();
     };
     while (bytes_for() > smem_limit) {
         int big = -1;
@@ -115,6 +124,7 @@ void layout_job_smem(KJob &j, uint32_t smem_limit)
         if (big < 0) break;
         kind[big] = (kind[big] == kTabTripleSmem && j.zech2[big]) ? kTabDoubleSmem : kTabDoubleGlobal;
     }
+    if (bytes_for() > smem_limit) return false;
     uint32_t off = 0;
     for (uint32_t k = 0; k < kMaxG; ++k) {
         j.tab_kind[k] = k < j.g ? kind[k] : kTabDoubleGlobal;
@@ -127,7 +137,19 @@ void layout_job_smem(KJob &j, uint32_t smem_limit)
         j.coef_off[k] = off32;
         if (k < j.g) off32 += ((j.q + 3) / 4) * 4;
     }
-    j.smem_bytes = off32 * 4;
+    uint32_t bytes = off32 * 4;   // multiple of 16
+    for (uint32_t k = 0; k < kMaxG; ++k) {
+        j.row_off[k] = bytes;
+        j.zdig_off[k] = bytes;
+        if (j.method == 1 && k < j.g) {
+            bytes += 4 * j.words * j.L[k];
+            bytes = (bytes + 15) / 16 * 16;
+            j.zdig_off[k] = bytes;
+            bytes += ((j.q + 15) / 16) * 16;
+        }
+    }
+    j.smem_bytes = bytes;
+    return true;
 }
 
 static uint32_t next_pow2(uint64_t v)
@@ -156,7 +178,7 @@ struct HostJob {
     uint64_t fam_n;
 };
 
-int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n)
+int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n, uint32_t flags)
 {
     int rc = validate_job(jb, fam_n);
     if (rc) return rc;
@@ -174,6 +196,8 @@ int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n)
     upow(jb.q, kj.d - 1, &kj.fam_mz);
     kj.qd = kj.fam_mz * jb.q;
     kj.n_tiles = (jb.count + kTileMembers - 1) / kTileMembers;
+    // enumerated families with q <= 63: groups of q members share all but c_0
+    const bool fan = !(flags & HWC_FLAG_HORNER) && jb.family.kind != HWC_FAM_MONIC_NOSUB_SAMPLED && jb.q <= 63;
     for (uint32_t k = 1; k <= jb.g; ++k) {
         const Tables *t = nullptr;
         rc = tables_cached(jb.q, k, &t);
@@ -185,8 +209,24 @@ int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n)
         kj.zech3[k - 1] = t->d_zech3;
         kj.zech2w[k - 1] = t->d_zech2w;
         kj.coef_log[k - 1] = t->d_coef_log;
+        kj.rows[k - 1] = jb.q <= 31 ? (const void *)t->d_rows32 : (const void *)t->d_rows64;
+        kj.zdig[k - 1] = t->d_zdig;
+        const uint32_t sdiv = t->L / (jb.q - 1);
+        kj.zdiv[k - 1] = (uint32_t)(((1ull << 32) + sdiv - 1) / sdiv);
     }
-    layout_job_smem(kj, std::min<uint32_t>(device_smem_optin(), 200u * 1024u));
+    const uint32_t limit = device_smem_optin() - 4096;   // static smem of the kernels
+    if (fan) {
+        kj.method = 1;
+        kj.words = jb.q <= 31 ? 1 : 2;
+        kj.first_group = jb.first / jb.q;
+        kj.n_tiles = jb.count ? (jb.first + jb.count - 1) / jb.q - kj.first_group + 1 : 0;
+        if (layout_job_smem(kj, limit)) return HWC_OK;
+        kj.method = 0;   // rows do not fit: per-member Horner
+        kj.words = 0;
+        kj.first_group = 0;
+        kj.n_tiles = (jb.count + kTileMembers - 1) / kTileMembers;
+    }
+    layout_job_smem(kj, limit);
     return HWC_OK;
 }
 
@@ -256,6 +296,7 @@ hwc_hist *hwc::hist_from_keys(const KJob &kj, const unsigned long long *keys,
 // the degree); a batch holds one group per distinct degree.
 struct BatchGroup {
     int D = 0;
+    uint32_t method = 0, words = 0;
     uint32_t first = 0, n = 0;       // jobs[first .. first+n) (sorted by degree)
     uint32_t start_off = 0;          // offset of this group's item table
     uint64_t n_items = 0;
@@ -334,8 +375,8 @@ static int batch_enqueue(hwc_batch *b, cudaStream_t s, bool capturing)
     } else {
         for (size_t g = 0; g < b->groups.size(); ++g) {
             const BatchGroup &G = b->groups[g];
-            rc = launch_persistent(G.D, b->d_jobs + G.first, b->d_item_start + G.start_off, G.n,
-                                   G.n_items, b->d_counters + g, G.max_smem, G.shape, s);
+            rc = launch_persistent(G.D, G.method, G.words, b->d_jobs + G.first, b->d_item_start + G.start_off,
+                                   G.n, G.n_items, b->d_counters + g, G.max_smem, G.shape, s);
             if (rc) return rc;
         }
     }
@@ -345,13 +386,15 @@ static int batch_enqueue(hwc_batch *b, cudaStream_t s, bool capturing)
 }
 
 // threads per CTA that maximise resident warps per SM for this degree and smem
-int hwc::choose_shape(int D, uint32_t smem, bool persistent, LaunchShape *out)
+int hwc::choose_shape(int D, uint32_t method, uint32_t words, uint32_t smem, bool persistent, LaunchShape *out)
 {
     const int sms = device_sm_count();
     int best_block = 256, best_warps = -1, best_ctas = 1;
-    for (int block : {256, 128}) {
+    const int blocks[2] = {256, 128};
+    for (int bi = 0; bi < (method == 1 ? 1 : 2); ++bi) {
+        const int block = blocks[bi];
         int ctas = 0;
-        int rc = max_ctas_per_sm(D, block, smem, persistent, &ctas);
+        int rc = max_ctas_per_sm(D, method, words, block, smem, persistent, &ctas);
         if (rc) return rc;
         const int warps = ctas * block / 32;
         if (warps > best_warps) {
@@ -363,7 +406,7 @@ int hwc::choose_shape(int D, uint32_t smem, bool persistent, LaunchShape *out)
     if (best_warps <= 0) return set_error(HWC_ERR_TOO_LARGE, "no CTA fits %u bytes of shared memory", smem);
     out->block = best_block;
     out->grid = sms * best_ctas;
-    out->item_tiles = (best_block / 32) * 2;
+    out->item_tiles = (best_block / 32) * (method == 1 ? 1 : 2);
     return HWC_OK;
 }
 
@@ -385,8 +428,13 @@ static int batch_create_impl(const hwc_job_t *jobs, size_t n, uint32_t flags, ui
     // order jobs by degree (stable), remember where each caller's job went
     std::vector<size_t> order(n);
     std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(),
-                     [&](size_t x, size_t y) { return jobs[x].family.degree < jobs[y].family.degree; });
+    // group key: degree, then kernel (fan-out for enumerated q <= 63 unless forced)
+    auto gkey = [&](size_t x) {
+        const hwc_job_t &j = jobs[x];
+        const bool fan = !(flags & HWC_FLAG_HORNER) && j.family.kind != HWC_FAM_MONIC_NOSUB_SAMPLED && j.q <= 63;
+        return std::make_tuple(j.family.degree, fan ? 1u : 0u, fan ? (j.q <= 31 ? 1u : 2u) : 0u);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return gkey(x) < gkey(y); });
     b->pos.resize(n);
     b->jobs.resize(n);
     for (size_t r = 0; r < n; ++r) {
@@ -394,7 +442,7 @@ static int batch_create_impl(const hwc_job_t *jobs, size_t n, uint32_t flags, ui
         b->pos[i] = r;
         HostJob &hj = b->jobs[r];
         hj.job = jobs[i];
-        rc = fill_kjob(jobs[i], hj.kj, &hj.fam_n);
+        rc = fill_kjob(jobs[i], hj.kj, &hj.fam_n, flags);
         if (rc) { batch_release(b); return rc; }
         KJob &kj = hj.kj;
         const uint32_t cap = hash_capacity(kj.g, kj.q, jobs[i].count, cap_scale);
@@ -405,9 +453,12 @@ static int batch_create_impl(const hwc_job_t *jobs, size_t n, uint32_t flags, ui
             batch_release(b);
             return rc;
         }
-        if (b->groups.empty() || b->groups.back().D != (int)kj.d) {
+        if (b->groups.empty() || b->groups.back().D != (int)kj.d || b->groups.back().method != kj.method ||
+            b->groups.back().words != kj.words) {
             BatchGroup G;
             G.D = (int)kj.d;
+            G.method = kj.method;
+            G.words = kj.words;
             G.first = (uint32_t)r;
             b->groups.push_back(G);
         }
@@ -418,7 +469,10 @@ static int batch_create_impl(const hwc_job_t *jobs, size_t n, uint32_t flags, ui
     const bool persistent = !(flags & HWC_FLAG_PLAIN);
     std::vector<uint64_t> starts;
     for (BatchGroup &G : b->groups) {
-        if ((rc = choose_shape(G.D, G.max_smem, persistent, &G.shape))) { batch_release(b); return rc; }
+        if ((rc = choose_shape(G.D, G.method, G.words, G.max_smem, persistent, &G.shape))) {
+            batch_release(b);
+            return rc;
+        }
         // work items: each job is cut into items of item_tiles tiles, in job order
         G.start_off = (uint32_t)starts.size();
         uint64_t acc = 0;
@@ -612,8 +666,8 @@ extern "C" int hwc_count(uint32_t g, uint32_t q, const hwc_family_t *fam, uint64
 }
 
 extern "C" int hwc_count_members(uint32_t g, uint32_t q, const hwc_family_t *fam, uint64_t first,
-                                 uint64_t count, int unfiltered, void *stream, int32_t *counts,
-                                 uint8_t *sqf)
+                                 uint64_t count, int unfiltered, uint32_t flags, void *stream,
+                                 int32_t *counts, uint8_t *sqf)
 {
     if (!fam || (count && (!counts || !sqf))) return set_error(HWC_ERR_ARG, "null argument");
     hwc_job_t j{};
@@ -628,7 +682,7 @@ extern "C" int hwc_count_members(uint32_t g, uint32_t q, const hwc_family_t *fam
     rc = prepare_count_kernels();
     if (rc) return rc;
     KJob kj;
-    rc = fill_kjob(j, kj, &fam_n);
+    rc = fill_kjob(j, kj, &fam_n, flags & HWC_FLAG_HORNER);
     if (rc) return rc;
     if (count == 0) return HWC_OK;
     kj.unfiltered = unfiltered ? 1u : 0u;
@@ -646,7 +700,7 @@ extern "C" int hwc_count_members(uint32_t g, uint32_t q, const hwc_family_t *fam
         return set_error(HWC_ERR_CUDA, "setup: %s", cudaGetErrorString(ce));
     }
     LaunchShape sh;
-    rc = choose_shape((int)kj.d, kj.smem_bytes, false, &sh);
+    rc = choose_shape((int)kj.d, kj.method, kj.words, kj.smem_bytes, false, &sh);
     if (rc == HWC_OK) rc = launch_plain(b->d_jobs, kj, sh, s);
     if (rc == HWC_OK) {
         ce = cudaMemcpyAsync(counts, kj.member_counts, count * g * sizeof(int32_t), cudaMemcpyDeviceToHost, s);

@@ -86,15 +86,15 @@ int ralloc(Request *r, T **p, uint64_t n)
     return HWC_OK;
 }
 
-int shape_for(hwc_server *s, int D, uint32_t smem, LaunchShape *out)
+int shape_for(hwc_server *s, int D, uint32_t method, uint32_t words, uint32_t smem, LaunchShape *out)
 {
-    auto key = std::make_pair(D, smem);
+    auto key = std::make_pair(D * 16 + (int)(method * 4 + words), smem);
     auto it = s->shapes.find(key);
     if (it != s->shapes.end()) {
         *out = it->second;
         return HWC_OK;
     }
-    int rc = choose_shape(D, smem, true, out);
+    int rc = choose_shape(D, method, words, smem, true, out);
     if (rc) return rc;
     s->shapes[key] = *out;
     return HWC_OK;
@@ -194,14 +194,16 @@ void server_loop(hwc_server *s)
 
         // one device step: a fair share of tiles of every active request; requests
         // of one degree share a persistent launch
+        auto skey = [](const Request *x) { return std::make_tuple(x->kj.d, x->kj.method, x->kj.words); };
         std::stable_sort(step.begin(), step.end(),
-                         [](const Request *x, const Request *y) { return x->kj.d < y->kj.d; });
+                         [&](const Request *x, const Request *y) { return skey(x) < skey(y); });
         const uint32_t n = (uint32_t)step.size();
         std::vector<uint64_t> took(n, 0);
         int rc = HWC_OK;
         uint32_t item_off = 0, ngroups = 0;
         struct StepGroup {
             int D;
+            uint32_t method, words;
             uint32_t first, n, off;
             uint64_t items;
             uint32_t smem;
@@ -211,9 +213,10 @@ void server_loop(hwc_server *s)
         for (uint32_t i = 0; i < n && rc == HWC_OK;) {
             uint32_t e = i;
             uint32_t smem = 0;
-            while (e < n && step[e]->kj.d == step[i]->kj.d) smem = std::max(smem, step[e++]->kj.smem_bytes);
-            StepGroup G{(int)step[i]->kj.d, i, e - i, item_off, 0, smem, LaunchShape()};
-            rc = shape_for(s, G.D, smem, &G.sh);
+            while (e < n && skey(step[e]) == skey(step[i])) smem = std::max(smem, step[e++]->kj.smem_bytes);
+            StepGroup G{(int)step[i]->kj.d, step[i]->kj.method, step[i]->kj.words, i, e - i, item_off, 0, smem,
+                        LaunchShape()};
+            rc = shape_for(s, G.D, G.method, G.words, smem, &G.sh);
             if (rc) break;
             uint64_t budget = s->cfg.step_items ? s->cfg.step_items : (uint64_t)G.sh.grid * 4;
             budget *= (uint64_t)G.sh.item_tiles;
@@ -225,8 +228,13 @@ void server_loop(hwc_server *s)
                 const uint64_t left = q->kj.n_tiles - q->next_tile;
                 const uint64_t t = std::min(left, share);
                 took[r] = t;
-                sl.first = q->kj.first + q->next_tile * kTileMembers;
-                sl.count = std::min<uint64_t>(q->kj.count - q->next_tile * kTileMembers, t * kTileMembers);
+                if (q->kj.method == 1) {
+                    // fan-out tiles are groups; the member range stays the request's
+                    sl.first_group = q->kj.first_group + q->next_tile;
+                } else {
+                    sl.first = q->kj.first + q->next_tile * kTileMembers;
+                    sl.count = std::min<uint64_t>(q->kj.count - q->next_tile * kTileMembers, t * kTileMembers);
+                }
                 sl.n_tiles = t;
                 s->h_jobs[r] = sl;
                 s->h_item_start[item_off + (r - i)] = items;
@@ -251,8 +259,8 @@ void server_loop(hwc_server *s)
         }
         for (size_t g = 0; rc == HWC_OK && g < groups.size(); ++g) {
             const StepGroup &G = groups[g];
-            rc = launch_persistent(G.D, s->d_jobs + G.first, s->d_item_start + G.off, G.n, G.items,
-                                   s->d_counters + g, G.smem, G.sh, s->stream);
+            rc = launch_persistent(G.D, G.method, G.words, s->d_jobs + G.first, s->d_item_start + G.off, G.n,
+                                   G.items, s->d_counters + g, G.smem, G.sh, s->stream);
         }
         if (rc == HWC_OK) {
             ce = cudaStreamSynchronize(s->stream);
@@ -316,7 +324,7 @@ extern "C" int hwc_serve_submit(hwc_server_t *s, const hwc_job_t *job, uint64_t 
     Request *r = new Request();
     r->job = *job;
     uint64_t fam_n = 0;
-    int rc = fill_kjob(*job, r->kj, &fam_n);   // validates, builds tables
+    int rc = fill_kjob(*job, r->kj, &fam_n, 0);   // validates, builds tables
     if (rc) {
         delete r;
         return rc;

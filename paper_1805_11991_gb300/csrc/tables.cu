@@ -279,6 +279,38 @@ __global__ void k_zech(uint32_t p, uint32_t L, const uint32_t *__restrict__ anti
     }
 }
 
+// fan-out rows: bit c of row l = [chi(alpha^l + e_c) = -1], e_c the digit c in F_Q;
+// alpha^l + e_c = e_c (1 + alpha^(l - log e_c)).  Top bit: alpha^l + e_c = 0 for
+// some c (then alpha^l lies in F_q^x).
+__global__ void k_rows(uint32_t q, uint32_t L, const uint32_t *__restrict__ zech,
+                       const uint32_t *__restrict__ coef_log, uint32_t *rows32,
+                       unsigned long long *rows64)
+{
+    for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < L; l += gridDim.x * blockDim.x) {
+        unsigned long long m = l & 1u;   // c = 0: chi(alpha^l) = (-1)^l
+        bool zero = false;
+        for (uint32_t c = 1; c < q; ++c) {
+            const uint32_t lc = coef_log[c];
+            const uint32_t n = l >= lc ? l - lc : l + L - lc;
+            const uint32_t z = zech[n];
+            if (z == L) zero = true;
+            else if ((lc + z) & 1u) m |= 1ull << c;
+        }
+        if (rows32) rows32[l] = (uint32_t)m | (zero ? 0x80000000u : 0u);
+        if (rows64) rows64[l] = m | (zero ? (1ull << 63) : 0ull);
+    }
+}
+
+// zdig[m]: the digit c with alpha^(m s) + e_c = 0, s = L/(q-1)
+__global__ void k_zdig(uint32_t q, uint32_t L, const uint32_t *__restrict__ coef_log, uint8_t *zdig)
+{
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c == 0 || c >= q) return;
+    const uint32_t s = L / (q - 1);
+    const uint32_t l = (coef_log[c] + L / 2) % L;   // log(-e_c)
+    zdig[l / s] = (uint8_t)c;
+}
+
 struct ElemArgs {
     uint32_t p, e, q, n, L;
     uint32_t mq[kMaxE + 1];
@@ -345,6 +377,9 @@ void tables_destroy(Tables *t)
     cudaFree(t->d_zech2);
     cudaFree(t->d_zech2w);
     cudaFree(t->d_zech3);
+    cudaFree(t->d_rows32);
+    cudaFree(t->d_rows64);
+    cudaFree(t->d_zdig);
     if (t->device >= 0 && t->device != cur && cur >= 0) cudaSetDevice(cur);
     delete t;
 }
@@ -447,6 +482,20 @@ int tables_build(uint32_t q, uint32_t k, Tables **out)
         th = (uint64_t)(L / (q - 1)) * bt % L;
     }
     k_coef_log<<<(q + 127) / 128, 128>>>(ea, th, t->d_antilog, t->d_log, t->d_coef_log);
+
+    // 4. fan-out rows (digits fit a 64-bit row)
+    if (q <= 63) {
+        bool rok = cudaMalloc(&t->d_zdig, q) == cudaSuccess;
+        if (rok && q <= 31) rok = cudaMalloc(&t->d_rows32, sizeof(uint32_t) * L) == cudaSuccess;
+        if (rok) rok = cudaMalloc(&t->d_rows64, sizeof(unsigned long long) * L) == cudaSuccess;
+        if (!rok) {
+            cudaFree(d_best);
+            return fail(set_error(HWC_ERR_NOMEM, "cudaMalloc of fan-out rows for Q=%u failed", t->Q));
+        }
+        k_rows<<<std::max(1u, std::min(4096u, (L + 255) / 256)), 256>>>(q, L, t->d_zech, t->d_coef_log,
+                                                                         t->d_rows32, t->d_rows64);
+        k_zdig<<<1, 64>>>(q, L, t->d_coef_log, t->d_zdig);
+    }
     cudaError_t ce = cudaDeviceSynchronize();
     cudaFree(d_best);
     if (ce != cudaSuccess) return fail(set_error(HWC_ERR_CUDA, "table kernels: %s", cudaGetErrorString(ce)));

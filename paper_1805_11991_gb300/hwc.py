@@ -75,7 +75,7 @@ def load(build_if_missing: bool = True):
             "hwc_tables_free": (None, [vp]),
             "hwc_family_size": (c_int, [u32, P(Family), P(u64)]),
             "hwc_count": (c_int, [u32, u32, P(Family), u64, u64, u32, vp, P(vp)]),
-            "hwc_count_members": (c_int, [u32, u32, P(Family), u64, u64, c_int, vp,
+            "hwc_count_members": (c_int, [u32, u32, P(Family), u64, u64, c_int, u32, vp,
                                           P(ctypes.c_int32), P(ctypes.c_uint8)]),
             "hwc_hist_size": (c_int, [vp, P(u64), P(u64), P(u64)]),
             "hwc_hist_genus": (c_int, [vp, P(u32)]),
@@ -214,12 +214,13 @@ def count(g: int, q: int, fam: Family, first: int, n: int, flags: int = 0, strea
     return _take_hist(h)
 
 
-def count_members(g: int, q: int, fam: Family, first: int, n: int, unfiltered: bool = False, stream=None):
+def count_members(g: int, q: int, fam: Family, first: int, n: int, unfiltered: bool = False,
+                  flags: int = 0, stream=None):
     """hwc_count_members: (counts int32[n, g], sqf uint8[n])."""
     load()
     counts = np.zeros((n, g), np.int32)
     sqf = np.zeros(n, np.uint8)
-    _check(_lib.hwc_count_members(g, q, ctypes.byref(fam), first, n, 1 if unfiltered else 0,
+    _check(_lib.hwc_count_members(g, q, ctypes.byref(fam), first, n, 1 if unfiltered else 0, flags,
                                   _stream_ptr(stream),
                                   counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                   sqf.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))))

@@ -17,9 +17,9 @@ def gpu_hist(spec: JobSpec, flags: int = 0):
     return hwc.count(spec.g, spec.q, j.family, spec.first, spec.n(), flags)
 
 
-def gpu_members(spec: JobSpec, unfiltered: bool = False):
+def gpu_members(spec: JobSpec, unfiltered: bool = False, flags: int = 0):
     j = to_job(spec)
-    return hwc.count_members(spec.g, spec.q, j.family, spec.first, spec.n(), unfiltered)
+    return hwc.count_members(spec.g, spec.q, j.family, spec.first, spec.n(), unfiltered, flags)
 
 
 def oracle_members(orc, spec: JobSpec, filter: bool = True):

@@ -40,7 +40,11 @@ def test_batch_equals_alone(flags):
             _same(b.result(i), alone[i])
         assert b.kernel_ms() > 0
     n = b.kernel_launches()
-    assert n == (2 + len(MIX) if flags & hwc.FLAG_PLAIN else 3)
+    def key(s):
+        fan = s.kind != MONIC_NOSUB_SAMPLED and s.q <= 63
+        return (s.degree, fan, (1 if s.q <= 31 else 2) if fan else 0)
+    groups = len({key(s) for s in MIX})
+    assert n == (2 + len(MIX) if flags & hwc.FLAG_PLAIN else 2 + groups)
     b.close()
 
 

@@ -51,10 +51,17 @@ MEMBER_CASES = [
 
 @pytest.mark.parametrize("spec", MEMBER_CASES, ids=lambda s: f"g{s.g}q{s.q}k{s.kind}d{s.degree}@{s.first}+{s.n()}")
 @pytest.mark.parametrize("unfiltered", [False, True])
-def test_members_match_oracle(orc, spec, unfiltered):
+@pytest.mark.parametrize("kernel", ["auto", "horner"])
+def test_members_match_oracle(orc, spec, unfiltered, kernel):
+    """'auto' takes the c_0 fan-out kernel for enumerated families with
+    q <= 63 and the per-member Horner kernel otherwise; 'horner' forces the
+    latter everywhere."""
     if unfiltered and spec.q > 100:
         pytest.skip("one mode is enough for the slow oracle field")
-    gc, gs = gpu_members(spec, unfiltered=unfiltered)
+    if kernel == "horner" and (spec.kind == MONIC_NOSUB_SAMPLED or spec.q > 63):
+        pytest.skip("same kernel as 'auto'")
+    flags = hwc.FLAG_HORNER if kernel == "horner" else 0
+    gc, gs = gpu_members(spec, unfiltered=unfiltered, flags=flags)
     oc, os_ = oracle_members(orc, spec, filter=not unfiltered)
     np.testing.assert_array_equal(gs, os_)
     np.testing.assert_array_equal(gc, oc)
@@ -65,8 +72,9 @@ def test_members_match_oracle(orc, spec, unfiltered):
     JobSpec(3, 7, MONIC_NOSUB, 7), JobSpec(2, 9, ALL_DEG, 5), JobSpec(4, 3, MONIC_NOSUB, 9),
     JobSpec(2, 31, MONIC_NOSUB, 6, 20_000_000, 300_001),
 ], ids=lambda s: f"g{s.g}q{s.q}d{s.degree}@{s.first}")
-def test_full_histograms_match_oracle(orc, spec):
-    h = gpu_hist(spec)
+@pytest.mark.parametrize("flags", [0, hwc.FLAG_HORNER], ids=["auto", "horner"])
+def test_full_histograms_match_oracle(orc, spec, flags):
+    h = gpu_hist(spec, flags)
     assert_hist_equal(h, oracle_hist(orc, spec))
     assert h.n_total == spec.n()
 
@@ -76,21 +84,29 @@ def test_empty_range():
     assert h.n_total == 0 and h.n_squarefree == 0 and len(h.mult) == 0
 
 
-def test_last_member_and_single_member(orc):
-    for spec in (JobSpec(2, 31, MONIC_NOSUB, 5, 31 ** 4 - 1, 1), JobSpec(2, 3, ALL_DEG, 5, 0, 1)):
-        gc, gs = gpu_members(spec, unfiltered=True)
+@pytest.mark.parametrize("flags", [0, hwc.FLAG_HORNER], ids=["auto", "horner"])
+def test_edge_ranges(orc, flags):
+    """Last member, single members, and ranges that start and end inside a
+    group of q members sharing c_1..c_d (partial fan-out groups)."""
+    for spec in (JobSpec(2, 31, MONIC_NOSUB, 5, 31 ** 4 - 1, 1), JobSpec(2, 3, ALL_DEG, 5, 0, 1),
+                 JobSpec(2, 31, MONIC_NOSUB, 5, 31 * 100 + 7, 31 * 3 + 11),
+                 JobSpec(2, 61, MONIC_NOSUB, 5, 61 * 7 + 40, 61 * 2 + 5),
+                 JobSpec(2, 37, MONIC_NOSUB, 6, 37 ** 4 + 30, 20),
+                 JobSpec(3, 13, MONIC_NOSUB, 7, 13 ** 5 + 12, 2)):
+        gc, gs = gpu_members(spec, unfiltered=True, flags=flags)
         oc, os_ = oracle_members(orc, spec, filter=False)
         np.testing.assert_array_equal(gc, oc)
         np.testing.assert_array_equal(gs, os_)
 
 
 @pytest.mark.parametrize("g,q,d", [(2, 5, 5), (2, 3, 6), (3, 3, 7), (2, 7, 6)])
-def test_character_sum_identity_on_gpu(g, q, d):
+@pytest.mark.parametrize("flags", [0, hwc.FLAG_HORNER], ids=["auto", "horner"])
+def test_character_sum_identity_on_gpu(g, q, d, flags):
     """Unfiltered whole MZ_d family: sum_f sum_x chi(f(x)) = sum over m | k with
     k/m even of N_m q^(d-1-m) (q^m - 1) (N_m = elements of degree exactly m)."""
     from test_oracle_invariants import _mobius
     spec = JobSpec(g, q, MONIC_NOSUB, d)
-    counts, _ = gpu_members(spec, unfiltered=True)
+    counts, _ = gpu_members(spec, unfiltered=True, flags=flags)
     for k in range(1, g + 1):
         Q = q ** k
         inf = 1 if d == 2 * g + 1 else 2
