@@ -53,11 +53,25 @@ def evals_per_member(spec: JobSpec) -> int:
     return spec.nominal_evals_per_member()
 
 
-def lookups_per_eval(spec: JobSpec) -> float:
-    """Zech lookups per point evaluation of the Horner chain: one per nonzero
-    coefficient among c_0..c_{d-2} (c_{d-1} = 0, lead 1), i.e. (d-1)(q-1)/q on
-    average over the family."""
-    return (spec.degree - 1) * (spec.q - 1) / spec.q
+def uses_fanout(spec: JobSpec) -> bool:
+    """The library takes the c_0 fan-out kernel for enumerated families with
+    q <= 63 and the per-member Horner kernel otherwise."""
+    return spec.kind != 2 and spec.q <= 63
+
+
+def table_reads(spec: JobSpec, n_squarefree: int) -> float:
+    """Shared-memory table reads one launch performs for this job (expected
+    value over the family):
+      per-member Horner: one Zech read per nonzero c_i, i <= d-2, per point,
+        (d-1)(q-1)/q per evaluation of a square-free member;
+      c_0 fan-out: per group of q members and point x, one Zech read per
+        nonzero c_i, 1 <= i <= d-2, plus one fan-out row: (d-2)(q-1)/q + 1."""
+    d, q = spec.degree, spec.q
+    pts = sum(q ** k - 1 for k in range(1, spec.g + 1))
+    if uses_fanout(spec):
+        groups = spec.n() / q
+        return groups * pts * ((d - 2) * (q - 1) / q + 1)
+    return n_squarefree * pts * (d - 1) * (q - 1) / q
 
 
 # ---------------------------------------------------------------------------
@@ -182,7 +196,7 @@ class ClockSampler:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("count_kernels.cu", "hwc_internal.cuh"):
+    for f in ("count_kernels.cu", "fanout_kernels.cu", "count_common.cuh", "hwc_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1805_11991_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -242,7 +256,7 @@ def main():
     sqf = [h.n_squarefree for h in results]
     units = sum(n * evals_per_member(s) for n, s in zip(sqf, jobs))
     members = sum(s.n() for s in jobs)
-    lookups = sum(n * evals_per_member(s) * lookups_per_eval(s) for n, s in zip(sqf, jobs))
+    lookups = sum(table_reads(s, n) for n, s in zip(sqf, jobs))
 
     def timed(batch, k):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
@@ -314,7 +328,7 @@ def main():
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps * batched.kernel_launches(),
         "roofline": {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "Glookup/s",
-                     "frac": achieved / peak, "traffic": traffic, "kernel": "k_persistent",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "k_fan_persistent" if all(uses_fanout(s) for s in jobs) else "k_persistent",
                      "kernel_ms": kern_ms,
                      "peak_source": f"{sms} SMs x {sm_max:.0f} MHz x 32 lanes (bank-conflict-free LDS)",
                      "measured_random_gather": measured,

@@ -213,7 +213,8 @@ __device__ __forceinline__ void row_of(const uint8_t *rows, const uint8_t *zdig,
         for (int w = 0; w < W; ++w) m[w] = 0;
     }
     n0 += (valid && zero_y) ? 1u : 0u;
-    if (live && flag) atomicAdd(&zc[zdig[__umulhi(yy, zdiv)]], 1u);
+    // l / s for l a multiple of s = L/(q-1); zdiv = 0 encodes s = 1 (k = 1)
+    if (live && flag) atomicAdd(&zc[zdig[zdiv ? __umulhi(yy, zdiv) : yy]], 1u);
 }
 
 // add 8 row words into the planes (carry-save tree, then ripple of the eights)
@@ -338,7 +339,19 @@ __device__ void process_group(const KJob &J, uint64_t gtile, const uint8_t *smem
             st.sqf += __popc(sm);
         }
     }
-    if ((J.unfiltered ? anyv : anys) == 0) return;
+    if ((J.unfiltered ? anyv : anys) == 0) {   // nothing to evaluate in this group
+        if (J.member_counts) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                if (!valid[w]) continue;
+                const uint64_t m = base + (uint32_t)lane + 32u * w - J.first;
+#pragma unroll
+                for (int k = 0; k < G; ++k) J.member_counts[m * G + k] = 0;
+                J.member_sqf[m] = 0;
+            }
+        }
+        return;
+    }
 
     int32_t N[W][G];
 #pragma unroll

@@ -211,8 +211,10 @@ int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n, uint32_t flags)
         kj.coef_log[k - 1] = t->d_coef_log;
         kj.rows[k - 1] = jb.q <= 31 ? (const void *)t->d_rows32 : (const void *)t->d_rows64;
         kj.zdig[k - 1] = t->d_zdig;
+        // ceil(2^32 / s) recovers l / s exactly for multiples l of s = L/(q-1) < 2^32;
+        // s = 1 (k = 1) is encoded as 0
         const uint32_t sdiv = t->L / (jb.q - 1);
-        kj.zdiv[k - 1] = (uint32_t)(((1ull << 32) + sdiv - 1) / sdiv);
+        kj.zdiv[k - 1] = sdiv == 1 ? 0u : (uint32_t)(((1ull << 32) + sdiv - 1) / sdiv);
     }
     const uint32_t limit = device_smem_optin() - 4096;   // static smem of the kernels
     if (fan) {
