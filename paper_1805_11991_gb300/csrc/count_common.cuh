@@ -230,6 +230,15 @@ __device__ void stage_job(const KJob &J, uint8_t *smem)
             for (uint32_t i = threadIdx.x; i + 1 < J.q; i += blockDim.x) zd[i] = J.zdig[k][i];
         }
     }
+    if (J.method == 1) {   // F_q digit arithmetic: mul | sub | inv
+        const uint32_t qq = J.q * J.q;
+        uint8_t *d = smem + J.fq_off;
+        for (uint32_t i = threadIdx.x; i < qq; i += blockDim.x) {
+            d[i] = J.fq_mul[i];
+            d[qq + i] = J.fq_sub[i];
+        }
+        for (uint32_t i = threadIdx.x; i < J.q; i += blockDim.x) d[2 * qq + i] = J.fq_inv[i];
+    }
 }
 
 __device__ __forceinline__ void flush_stats(const KJob &J, WarpStats &st, int lane)

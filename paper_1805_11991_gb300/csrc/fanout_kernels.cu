@@ -26,6 +26,11 @@ namespace {
 constexpr int kFanWarps = 8;          // warps per CTA of the fan-out kernels
 constexpr uint32_t kChunkBlocks = 31; // 8-input blocks per lane before a flush (< 256 per plane set)
 
+// CTAs per SM the register allocation aims at: 3 where the chain is short
+// enough to stay in 80 registers without spilling, else 2
+template <int D, int W>
+constexpr int fan_min_ctas() { return (D <= 6 && W == 1) ? 3 : 2; }
+
 __device__ __forceinline__ void csa(uint32_t &h, uint32_t &l, uint32_t a, uint32_t b, uint32_t c)
 {
     const uint32_t u = a ^ b;
@@ -73,7 +78,7 @@ struct HChain {
     uint32_t gpi[D];     // per position: gap to the previous nonzero (0: no step)
     uint32_t lam_last;   // lam_{is}
     uint32_t tail;       // is: y = alpha^(lam_last + z + is*j)
-    int dense;           // 2: positions 1..D-2 all nonzero (c_{D-1} = 0); 1: 1..D-1; 0: general
+    int dense;           // 2: positions 1..D-2 all nonzero and c_{D-1} = 0; 0: general
     bool none;           // h = c_D x^(D-1)
 };
 
@@ -102,8 +107,7 @@ __device__ __forceinline__ void make_hchain(HChain<D> &H, const uint32_t (&lam)[
         }
     }
     const uint32_t full2 = ((1u << (D - 1)) - 1u) & ~1u;   // bits 1..D-2
-    const uint32_t full1 = ((1u << D) - 1u) & ~1u;         // bits 1..D-1
-    H.dense = (nzh == full2) ? 2 : (nzh == full1) ? 1 : 0;
+    H.dense = (nzh == full2) ? 2 : 0;
 }
 
 // log y for x = alpha^j (y = x h(x)), or L when y = 0; two x per lane.
@@ -134,13 +138,6 @@ __device__ __forceinline__ void log_y_pair(const Tab T, uint32_t L, uint32_t bar
     if (H.dense == 2) {
 #pragma unroll
         for (int i = D - 3; i >= 1; --i) {
-            const uint32_t zA = T[uA], zB = T[uB];
-            uA = chain_step<TRIPLE>(zA, H.dli[i], xA, L, cap);
-            uB = chain_step<TRIPLE>(zB, H.dli[i], xB, L, cap);
-        }
-    } else if (H.dense == 1) {
-#pragma unroll
-        for (int i = D - 2; i >= 1; --i) {
             const uint32_t zA = T[uA], zB = T[uB];
             uA = chain_step<TRIPLE>(zA, H.dli[i], xA, L, cap);
             uB = chain_step<TRIPLE>(zB, H.dli[i], xB, L, cap);
@@ -236,51 +233,157 @@ __device__ __forceinline__ void add8(Planes &P, const uint32_t (&a)[8])
     }
 }
 
-// sum the planes of the 32 lanes; lane c gets the count of bit position c
-__device__ __forceinline__ uint32_t reduce_planes(const Planes &P)
+// sum the planes of the 32 lanes; lane c gets the count of bit position c.
+// NB: planes 0..NB-1 are in use on entry (per-lane counts < 2^NB).
+template <int NB>
+__device__ __forceinline__ uint32_t reduce_planes(const uint32_t (&p)[8])
 {
-    uint32_t s[13];
+    uint32_t s[NB + 5];
 #pragma unroll
-    for (int b = 0; b < 8; ++b) s[b] = P.p[b];
-#pragma unroll
-    for (int b = 8; b < 13; ++b) s[b] = 0;
+    for (int b = 0; b < NB + 5; ++b) s[b] = b < NB ? p[b] : 0u;
 #pragma unroll
     for (int lvl = 0; lvl < 5; ++lvl) {
         const int off = 16 >> lvl;
-        const int nb = 8 + lvl;   // planes in use before this level
         uint32_t carry = 0;
 #pragma unroll
-        for (int b = 0; b < 13; ++b) {
-            if (b <= nb) {
-                const uint32_t o = __shfl_xor_sync(0xFFFFFFFFu, s[b], off);
-                const uint32_t x = s[b] ^ o;
-                const uint32_t nc = (s[b] & o) | (x & carry);
-                s[b] = x ^ carry;
-                carry = nc;
-            }
+        for (int b = 0; b <= NB + lvl; ++b) {
+            const uint32_t o = __shfl_xor_sync(0xFFFFFFFFu, s[b], off);
+            const uint32_t x = s[b] ^ o;
+            const uint32_t nc = (s[b] & o) | (x & carry);
+            s[b] = x ^ carry;
+            carry = nc;
         }
     }
     const int lane = threadIdx.x & 31;
     uint32_t cnt = 0;
 #pragma unroll
-    for (int b = 0; b < 13; ++b) cnt |= ((s[b] >> lane) & 1u) << b;
+    for (int b = 0; b < NB + 5; ++b) cnt |= ((s[b] >> lane) & 1u) << b;
     return cnt;
 }
 
-__device__ __forceinline__ void decode_index(const KJob &J, uint64_t idx, uint32_t *c, int D)
+template <int D>
+__device__ __forceinline__ void decode_index(const KJob &J, uint64_t idx, uint32_t (&c)[D + 1])
 {
     const uint32_t q = J.q;
-    const int ndig = (J.kind == HWC_FAM_ALL_DEG) ? D : D - 1;
+    const bool all = J.kind == HWC_FAM_ALL_DEG;
     uint64_t r = idx;
-    for (int i = 0; i < ndig; ++i) {
-        c[i] = (uint32_t)(r % q);
-        r /= q;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        if (i < D - 1 || all) {
+            if (r >> 32) {
+                c[i] = (uint32_t)(r % q);
+                r /= q;
+            } else {
+                const uint32_t r32 = (uint32_t)r;
+                c[i] = r32 % q;
+                r = r32 / q;
+            }
+        }
     }
-    if (J.kind == HWC_FAM_ALL_DEG) {
+    if (all) {
         c[D] = 1 + (uint32_t)r;
     } else {
         c[D - 1] = 0;
         c[D] = 1;
+    }
+}
+
+// square-freeness by Euclid's algorithm on gcd(f, f') with F_q digit tables
+// (a*b, a-b, 1/a) in shared memory
+template <int D>
+__device__ bool squarefree_digits(const uint8_t *mulT, const uint8_t *subT, const uint8_t *invT,
+                                  uint32_t q, uint32_t p, const uint32_t (&c)[D + 1])
+{
+    uint32_t P[2][D + 1];
+    int dg[2];
+#pragma unroll
+    for (int i = 0; i <= D; ++i) P[0][i] = c[i];
+    // f' = sum i c_i x^(i-1); the integer i is the digit (i mod p)
+#pragma unroll
+    for (int i = 1; i <= D; ++i) P[1][i - 1] = mulT[(i % p) * q + c[i]];
+    P[1][D] = 0;
+    dg[0] = D;
+    dg[1] = D - 1;
+    while (dg[0] >= 0 && P[0][dg[0]] == 0) --dg[0];
+    while (dg[1] >= 0 && P[1][dg[1]] == 0) --dg[1];
+    if (dg[1] < 0) return false;
+    int a = 0, b = 1;
+    while (dg[b] >= 0) {
+        const int db = dg[b];
+        const uint32_t il = invT[P[b][db]];
+        for (int t = dg[a]; t >= db; --t) {
+            const uint32_t at = P[a][t];
+            if (!at) continue;
+            const uint32_t cf = mulT[at * q + il];
+            for (int i = 0; i <= db; ++i)
+                P[a][t - db + i] = subT[P[a][t - db + i] * q + mulT[cf * q + P[b][i]]];
+        }
+        int da = db - 1;
+        while (da >= 0 && P[a][da] == 0) --da;
+        dg[a] = da;
+        const int tmp = a;
+        a = b;
+        b = tmp;
+    }
+    return dg[a] == 0;
+}
+
+// per-member counts of one field for the whole group: lane c gets sum_x chi(f_c(x))
+// for c = lane (and lane + 32), from n_0, the row-bit counts and z_c
+template <int D, int W, bool TRIPLE, class Tab>
+__device__ __forceinline__ void group_field(const Tab T, const KJob &J, int k, const uint8_t *smem,
+                                            const HChain<D> &H, const uint32_t (&lam)[D + 1], uint32_t nz,
+                                            uint32_t *zc, int lane, uint32_t &n0, uint32_t (&cnt)[W])
+{
+    const uint32_t L = J.L[k];
+    const uint8_t *rows = smem + J.row_off[k];
+    const uint8_t *zdig = smem + J.zdig_off[k];
+    const uint32_t zdiv = J.zdiv[k];
+    const uint32_t bar = J.barrett[k];
+    if (L <= 64) {   // tiny field (k = 1): one pair of x per lane, counts < 4
+        const uint32_t jA = lane, jB = lane + 32;
+        const bool vA = jA < L, vB = jB < L;
+        uint32_t yA, yB;
+        log_y_pair<D, TRIPLE>(T, L, bar, H, lam, nz, vA ? jA : 0, vB ? jB : 0, yA, yB);
+        uint32_t mA[W], mB[W];
+        row_of<W>(rows, zdig, zdiv, L, yA, vA, mA, n0, zc);
+        row_of<W>(rows, zdig, zdiv, L, yB, vB, mB, n0, zc);
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            uint32_t p2[8] = {mA[w] ^ mB[w], mA[w] & mB[w], 0, 0, 0, 0, 0, 0};
+            cnt[w] += reduce_planes<2>(p2);
+        }
+        return;
+    }
+    for (uint32_t c0 = 0; c0 < L; c0 += kChunkBlocks * 256) {
+        Planes P[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w)
+#pragma unroll
+            for (int b = 0; b < 8; ++b) P[w].p[b] = 0;
+        const uint32_t cend = min(L, c0 + kChunkBlocks * 256);
+        for (uint32_t j0 = c0; j0 < cend; j0 += 256) {
+            uint32_t a[W][8];
+#pragma unroll
+            for (int it = 0; it < 4; ++it) {
+                const uint32_t jA = j0 + it * 64 + lane, jB = jA + 32;
+                const bool vA = jA < cend, vB = jB < cend;
+                uint32_t yA, yB;
+                log_y_pair<D, TRIPLE>(T, L, bar, H, lam, nz, vA ? jA : 0, vB ? jB : 0, yA, yB);
+                uint32_t mA[W], mB[W];
+                row_of<W>(rows, zdig, zdiv, L, yA, vA, mA, n0, zc);
+                row_of<W>(rows, zdig, zdiv, L, yB, vB, mB, n0, zc);
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    a[w][2 * it] = mA[w];
+                    a[w][2 * it + 1] = mB[w];
+                }
+            }
+#pragma unroll
+            for (int w = 0; w < W; ++w) add8(P[w], a[w]);
+        }
+#pragma unroll
+        for (int w = 0; w < W; ++w) cnt[w] += reduce_planes<8>(P[w].p);
     }
 }
 
@@ -295,7 +398,7 @@ __device__ void process_group(const KJob &J, uint64_t gtile, const uint8_t *smem
     const uint64_t base = grp * q;
     // coefficients c_1..c_D of the group (every lane decodes the same index)
     uint32_t c[D + 1];
-    decode_index(J, base, c, D);
+    decode_index<D>(J, base, c);
     c[0] = 0;
     uint32_t nz = 0;
 #pragma unroll
@@ -303,9 +406,13 @@ __device__ void process_group(const KJob &J, uint64_t gtile, const uint8_t *smem
 
     const uint16_t *s16 = reinterpret_cast<const uint16_t *>(smem);
     const uint32_t *s32 = reinterpret_cast<const uint32_t *>(smem);
+    const uint8_t *mulT = smem + J.fq_off;
+    const uint8_t *subT = mulT + q * q;
+    const uint8_t *invT = subT + q * q;
 
     // this lane's members: c_0 = lane (and lane + 32)
     bool valid[W], sqf[W];
+    uint32_t anyv = 0, anys = 0;
 #pragma unroll
     for (int w = 0; w < W; ++w) {
         const uint32_t c0 = (uint32_t)lane + 32u * w;
@@ -317,23 +424,12 @@ __device__ void process_group(const KJob &J, uint64_t gtile, const uint8_t *smem
 #pragma unroll
             for (int i = 0; i <= D; ++i) cm[i] = c[i];
             cm[0] = c0;
-            const uint32_t *coef1 = s32 + J.coef_off[0];
-            if (J.tab_kind[0] != kTabDoubleGlobal) {
-                FqLog<TabS> F{TabS{s16 + J.tab_off[0]}, J.L[0]};
-                sqf[w] = squarefree<D>(F, coef1, J.p, cm);
-            } else {
-                FqLog<TabG> F{TabG{J.zech2w[0]}, J.L[0]};
-                sqf[w] = squarefree<D>(F, coef1, J.p, cm);
-            }
+            sqf[w] = squarefree_digits<D>(mulT, subT, invT, q, J.p, cm);
         }
-    }
-    uint32_t anyv = 0, anys = 0;
-#pragma unroll
-    for (int w = 0; w < W; ++w) {
-        anyv |= __ballot_sync(0xFFFFFFFFu, valid[w]);
-        anys |= __ballot_sync(0xFFFFFFFFu, sqf[w]);
         const unsigned vm = __ballot_sync(0xFFFFFFFFu, valid[w]);
         const unsigned sm = __ballot_sync(0xFFFFFFFFu, sqf[w]);
+        anyv |= vm;
+        anys |= sm;
         if (lane == 0) {
             st.examined += __popc(vm);
             st.sqf += __popc(sm);
@@ -363,11 +459,6 @@ __device__ void process_group(const KJob &J, uint64_t gtile, const uint8_t *smem
         for (int i = 0; i <= D; ++i) lam[i] = coefk[c[i]];
         HChain<D> H;
         make_hchain<D>(H, lam, nz, L);
-        const uint8_t *rows = smem + J.row_off[k];
-        const uint8_t *zdig = smem + J.zdig_off[k];
-        const uint32_t zdiv = J.zdiv[k];
-        const uint32_t kind = J.tab_kind[k];
-        const uint32_t bar = J.barrett[k];
         // clear the zero-correction counters of this warp
         zc[lane] = 0;
         zc[lane + 32] = 0;
@@ -375,42 +466,13 @@ __device__ void process_group(const KJob &J, uint64_t gtile, const uint8_t *smem
         uint32_t n0 = 0, cnt[W];
 #pragma unroll
         for (int w = 0; w < W; ++w) cnt[w] = 0;
-        for (uint32_t c0 = 0; c0 < L; c0 += kChunkBlocks * 256) {
-            Planes P[W];
-#pragma unroll
-            for (int w = 0; w < W; ++w)
-#pragma unroll
-                for (int b = 0; b < 8; ++b) P[w].p[b] = 0;
-            const uint32_t cend = min(L, c0 + kChunkBlocks * 256);
-            for (uint32_t j0 = c0; j0 < cend; j0 += 256) {
-                uint32_t a[W][8];
-#pragma unroll
-                for (int it = 0; it < 4; ++it) {
-                    const uint32_t jA = j0 + it * 64 + lane, jB = jA + 32;
-                    const bool vA = jA < cend, vB = jB < cend;
-                    const uint32_t xA = vA ? jA : 0, xB = vB ? jB : 0;
-                    uint32_t yA, yB;
-                    if (kind == kTabTripleSmem)
-                        log_y_pair<D, true>(TabS{s16 + J.tab_off[k]}, L, bar, H, lam, nz, xA, xB, yA, yB);
-                    else if (kind == kTabDoubleSmem)
-                        log_y_pair<D, false>(TabS{s16 + J.tab_off[k]}, L, bar, H, lam, nz, xA, xB, yA, yB);
-                    else
-                        log_y_pair<D, false>(TabG{J.zech2w[k]}, L, bar, H, lam, nz, xA, xB, yA, yB);
-                    uint32_t mA[W], mB[W];
-                    row_of<W>(rows, zdig, zdiv, L, yA, vA, mA, n0, zc);
-                    row_of<W>(rows, zdig, zdiv, L, yB, vB, mB, n0, zc);
-#pragma unroll
-                    for (int w = 0; w < W; ++w) {
-                        a[w][2 * it] = mA[w];
-                        a[w][2 * it + 1] = mB[w];
-                    }
-                }
-#pragma unroll
-                for (int w = 0; w < W; ++w) add8(P[w], a[w]);
-            }
-#pragma unroll
-            for (int w = 0; w < W; ++w) cnt[w] += reduce_planes(P[w]);
-        }
+        const uint32_t kind = J.tab_kind[k];
+        if (kind == kTabTripleSmem)
+            group_field<D, W, true>(TabS{s16 + J.tab_off[k]}, J, k, smem, H, lam, nz, zc, lane, n0, cnt);
+        else if (kind == kTabDoubleSmem)
+            group_field<D, W, false>(TabS{s16 + J.tab_off[k]}, J, k, smem, H, lam, nz, zc, lane, n0, cnt);
+        else
+            group_field<D, W, false>(TabG{J.zech2w[k]}, J, k, smem, H, lam, nz, zc, lane, n0, cnt);
         n0 = __reduce_add_sync(0xFFFFFFFFu, n0) + 1;   // + x = 0 (y = g(0) = 0)
         __syncwarp();
         int inf = 1;
@@ -453,7 +515,7 @@ __device__ void process_group(const KJob &J, uint64_t gtile, const uint8_t *smem
 }
 
 template <int D, int W>
-__global__ void __launch_bounds__(kFanWarps * 32) k_fan_plain(const KJob *__restrict__ jp)
+__global__ void __launch_bounds__(kFanWarps * 32, fan_min_ctas<D, W>()) k_fan_plain(const KJob *__restrict__ jp)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ uint32_t zc_all[kFanWarps][64];
@@ -468,7 +530,7 @@ __global__ void __launch_bounds__(kFanWarps * 32) k_fan_plain(const KJob *__rest
 }
 
 template <int D, int W>
-__global__ void __launch_bounds__(kFanWarps * 32) k_fan_persistent(const KJob *__restrict__ jobs,
+__global__ void __launch_bounds__(kFanWarps * 32, fan_min_ctas<D, W>()) k_fan_persistent(const KJob *__restrict__ jobs,
                                                                    const uint64_t *__restrict__ item_start,
                                                                    uint32_t n_jobs, uint64_t n_items,
                                                                    unsigned long long *counter,

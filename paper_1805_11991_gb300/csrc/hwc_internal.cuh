@@ -62,6 +62,10 @@ struct Tables {
     uint32_t *d_rows32 = nullptr;   // [L] when q <= 31
     unsigned long long *d_rows64 = nullptr;   // [L] when q <= 63
     uint8_t *d_zdig = nullptr;      // [q-1]
+    // F_q arithmetic on digits (k = 1, q <= 63): a*b, a-b (u8 [q*q]), 1/a (u8 [q])
+    uint8_t *d_fq_mul = nullptr;
+    uint8_t *d_fq_sub = nullptr;
+    uint8_t *d_fq_inv = nullptr;
 };
 
 // where a count kernel reads the Zech table of one field
@@ -108,6 +112,8 @@ struct KJob {
     uint32_t row_off[kMaxG];          // byte offset of the rows in smem
     uint32_t zdig_off[kMaxG];         // byte offset of zdig in smem
     uint32_t zdiv[kMaxG];             // ceil(2^32 / (L/(q-1))): l / s by a high multiply
+    const uint8_t *fq_mul, *fq_sub, *fq_inv;   // digit arithmetic of F_q (fan-out jobs)
+    uint32_t fq_off;                  // byte offset of mul | sub | inv in smem
     // outputs
     unsigned long long *hkeys;        // [hmask+1]
     unsigned long long *hcounts;      // [hmask+1]

@@ -110,7 +110,7 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit)
         if (j.method != 1) return 0;
         uint64_t b = 0;
         for (uint32_t k = 0; k < j.g; ++k) b += 4ull * j.words * j.L[k] + ((j.q + 15) / 16) * 16;
-        return b;
+        return b + ((2ull * j.q * j.q + j.q + 15) / 16) * 16;
     };
     auto bytes_for = [&](void) {
         uint64_t u16 = 0;
@@ -148,6 +148,8 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit)
             bytes += ((j.q + 15) / 16) * 16;
         }
     }
+    j.fq_off = bytes;
+    if (j.method == 1) bytes += ((2 * j.q * j.q + j.q + 15) / 16) * 16;
     j.smem_bytes = bytes;
     return true;
 }
@@ -210,6 +212,11 @@ int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n, uint32_t flags)
         kj.zech2w[k - 1] = t->d_zech2w;
         kj.coef_log[k - 1] = t->d_coef_log;
         kj.rows[k - 1] = jb.q <= 31 ? (const void *)t->d_rows32 : (const void *)t->d_rows64;
+        if (k == 1) {
+            kj.fq_mul = t->d_fq_mul;
+            kj.fq_sub = t->d_fq_sub;
+            kj.fq_inv = t->d_fq_inv;
+        }
         kj.zdig[k - 1] = t->d_zdig;
         // ceil(2^32 / s) recovers l / s exactly for multiples l of s = L/(q-1) < 2^32;
         // s = 1 (k = 1) is encoded as 0

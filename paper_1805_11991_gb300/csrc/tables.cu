@@ -311,6 +311,38 @@ __global__ void k_zdig(uint32_t q, uint32_t L, const uint32_t *__restrict__ coef
     zdig[l / s] = (uint8_t)c;
 }
 
+// digit arithmetic of F_q from its log tables (k = 1): e_a e_b, e_a - e_b, 1/e_a
+// as digits, through the inverse of the digit -> log map.
+__global__ void k_fq_digit_tables(uint32_t q, uint32_t L, const uint32_t *__restrict__ zech,
+                                  const uint32_t *__restrict__ coef_log, uint8_t *mul, uint8_t *sub,
+                                  uint8_t *inv)
+{
+    extern __shared__ uint8_t dig_of_log[];   // [L]
+    for (uint32_t c = threadIdx.x; c < q; c += blockDim.x)
+        if (c) dig_of_log[coef_log[c]] = (uint8_t)c;
+    __syncthreads();
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < q * q; i += gridDim.x * blockDim.x) {
+        const uint32_t a = i / q, b = i % q;
+        const uint32_t la = coef_log[a], lb = coef_log[b];
+        // product
+        mul[i] = (a == 0 || b == 0) ? 0 : dig_of_log[(la + lb) % L];
+        // difference a - b = a + (-1) b; log(-b) = lb + L/2
+        uint8_t d;
+        if (b == 0) d = (uint8_t)a;
+        else {
+            const uint32_t lnb = (lb + L / 2) % L;
+            if (a == 0) d = dig_of_log[lnb];
+            else {
+                // e_a + e_{-b} = e_a (1 + alpha^(lnb - la))
+                const uint32_t z = zech[(lnb + L - la) % L];
+                d = (z == L) ? 0 : dig_of_log[(la + z) % L];
+            }
+        }
+        sub[i] = d;
+        if (b == 0 && a < q) inv[a] = a == 0 ? 0 : dig_of_log[(L - la) % L];
+    }
+}
+
 struct ElemArgs {
     uint32_t p, e, q, n, L;
     uint32_t mq[kMaxE + 1];
@@ -380,6 +412,9 @@ void tables_destroy(Tables *t)
     cudaFree(t->d_rows32);
     cudaFree(t->d_rows64);
     cudaFree(t->d_zdig);
+    cudaFree(t->d_fq_mul);
+    cudaFree(t->d_fq_sub);
+    cudaFree(t->d_fq_inv);
     if (t->device >= 0 && t->device != cur && cur >= 0) cudaSetDevice(cur);
     delete t;
 }
@@ -495,6 +530,16 @@ int tables_build(uint32_t q, uint32_t k, Tables **out)
         k_rows<<<std::max(1u, std::min(4096u, (L + 255) / 256)), 256>>>(q, L, t->d_zech, t->d_coef_log,
                                                                          t->d_rows32, t->d_rows64);
         k_zdig<<<1, 64>>>(q, L, t->d_coef_log, t->d_zdig);
+        if (k == 1) {
+            rok = cudaMalloc(&t->d_fq_mul, q * q) == cudaSuccess && cudaMalloc(&t->d_fq_sub, q * q) == cudaSuccess &&
+                  cudaMalloc(&t->d_fq_inv, q) == cudaSuccess;
+            if (!rok) {
+                cudaFree(d_best);
+                return fail(set_error(HWC_ERR_NOMEM, "cudaMalloc of F_%u digit tables failed", q));
+            }
+            k_fq_digit_tables<<<(q * q + 255) / 256, 256, L>>>(q, L, t->d_zech, t->d_coef_log, t->d_fq_mul,
+                                                               t->d_fq_sub, t->d_fq_inv);
+        }
     }
     cudaError_t ce = cudaDeviceSynchronize();
     cudaFree(d_best);
