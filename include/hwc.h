@@ -221,6 +221,40 @@ int hwc_serve_latency(hwc_server_t *s, uint64_t ticket, double *queued_us,
 int hwc_serve_close(hwc_server_t *s);
 
 /* ------------------------------------------------------------------ */
+/* Counting without device allocation                                  */
+
+/* Histogram of one job for callers that cannot allocate device memory when
+ * they count (for example while a stream is being captured into a CUDA
+ * graph, or in a process that reserves device memory up front and forbids
+ * further cudaMalloc).  The paper has no counterpart; it is the count of
+ * hwc_count through the per-member kernel with its working memory in a fixed
+ * device array instead of allocations.
+ *  - Calls no cudaMalloc, cudaFree or other allocating routine.  The hash,
+ *    statistics and counters live in one file-scope device array of
+ *    HWC_NOALLOC_SCRATCH_BYTES (32768 hash slots, about 512 KiB), which every
+ *    GPU that loads the library holds until the process exits.
+ *  - The job must fit that array: jobs whose histogram could need more than
+ *    32768 hash slots (min(count, Hasse-Weil box) above 16384) are rejected
+ *    with HWC_ERR_TOO_LARGE before anything runs.
+ *  - tables[k-1] (k = 1..g) are handles from hwc_field_tables(q, k), built
+ *    beforehand; they are read, not changed.
+ *  - Outputs are DEVICE buffers owned by the caller: counts[max_entries*g]
+ *    (#C_1..#C_g per entry) and mult[max_entries], in hash order (not
+ *    sorted); n_out[3] = number of entries, square-free members, members
+ *    examined.  More than max_entries entries gives HWC_ERR_TOO_LARGE.
+ *  - The first call on a device sets the library up for it (the device
+ *    address of the array, kernel attributes); make that first call before
+ *    any stream capture.  Synchronous on `stream` (it waits to report
+ *    overflow).
+ *  - Every call shares the one array and clears it first, so calls that
+ *    overlap on the GPU (other streams, other host threads) race: run them
+ *    one after another. */
+#define HWC_NOALLOC_SCRATCH_BYTES (64u + 16u * 32768u)
+int hwc_count_noalloc(uint32_t g, uint32_t q, const hwc_family_t *fam, uint64_t first,
+                      uint64_t count, const hwc_tables_t *const *tables, uint64_t max_entries,
+                      int32_t *counts, uint64_t *mult, uint64_t *n_out, void *stream);
+
+/* ------------------------------------------------------------------ */
 /* Measurement                                                         */
 
 /* Rate of dependent, uniformly random 16-bit reads from a shared-memory

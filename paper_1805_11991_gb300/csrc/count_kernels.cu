@@ -26,6 +26,7 @@
 #include "count_common.cuh"
 
 #include <algorithm>
+#include <cstring>
 
 namespace hwc {
 namespace {
@@ -467,3 +468,217 @@ int launch_compact(const KJob *d_jobs, uint32_t n_jobs, cudaStream_t s)
 }
 
 }  // namespace hwc
+
+// ---------------------------------------------------------------------
+// Histogram without device allocation (hwc_count_noalloc).
+//
+// Some callers cannot call cudaMalloc when they count: code that runs while a
+// stream is being captured into a CUDA graph (allocation would break the
+// capture), processes that reserve all device memory up front and hand out
+// fixed pools, or host applications whose plug-in rules forbid device
+// allocation.  This entry point keeps all of its working memory in one
+// file-scope device array of fixed size: the histogram hash (keys and
+// counts), the member statistics and the entry counter.  The job descriptor
+// travels as a kernel parameter, the field tables are the caller's handles
+// built earlier, and the results go to device buffers the caller owns.
+
+namespace hwc {
+namespace {
+
+constexpr uint32_t kNoAllocSlots = 1u << 15;   // hash slots: distinct tuples < 16384
+// layout: stats[4] | entries | pad[3] | keys[kNoAllocSlots] | counts[kNoAllocSlots]
+constexpr size_t kNoAllocHeader = 8 * sizeof(unsigned long long);
+constexpr size_t kNoAllocBytes = kNoAllocHeader + 2 * sizeof(unsigned long long) * kNoAllocSlots;
+
+// one per device that loads the library; every call shares it
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+__global__ void k_na_clear(unsigned char *scratch, uint32_t slots)
+{
+    unsigned long long *hdr = reinterpret_cast<unsigned long long *>(scratch);
+    unsigned long long *keys = hdr + 8;
+    unsigned long long *cnts = keys + kNoAllocSlots;
+    if (blockIdx.x == 0 && threadIdx.x < 8) hdr[threadIdx.x] = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < slots; i += gridDim.x * blockDim.x) {
+        keys[i] = kEmptyKey;
+        cnts[i] = 0;
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_na_count(const KJob J)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    stage_job(J, smem);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    WarpStats st;
+    for (uint64_t t = (uint64_t)blockIdx.x * nw + warp; t < J.n_tiles; t += (uint64_t)gridDim.x * nw)
+        process_tile<D>(J, t, smem, lane, st);
+    flush_stats(J, st, lane);
+}
+
+// filled hash slots -> caller's (#C_1..#C_g, multiplicity) arrays, hash order
+__global__ void k_na_emit(const KJob J, int32_t *counts, uint64_t *mult, uint64_t max_entries)
+{
+    unsigned long long *entries = J.stats + 4;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= J.hmask; i += gridDim.x * blockDim.x) {
+        const unsigned long long key = J.hkeys[i];
+        if (key == kEmptyKey) continue;
+        const unsigned long long o = atomicAdd(entries, 1ull);
+        if (o >= max_entries) continue;
+        for (uint32_t k = 0; k < J.g; ++k) {
+            const int a = (int)((key >> (16 * k)) & 0xFFFFu) - 32768;
+            counts[o * J.g + k] = (int32_t)J.Q[k] + 1 - a;   // #C = Q + 1 - a (eq. 1.1)
+        }
+        mult[o] = J.hcounts[i];
+    }
+}
+
+// n_out[0..2] = entries, square-free members, members examined
+__global__ void k_na_finish(const KJob J, uint64_t *n_out)
+{
+    if (threadIdx.x == 0) {
+        n_out[0] = J.stats[4];
+        n_out[1] = J.stats[1];
+        n_out[2] = J.stats[0];
+    }
+}
+
+template <int D>
+KernelFn na_count_fn()
+{
+    return (KernelFn)k_na_count<D>;
+}
+
+KernelFn na_count_kernel(int D)
+{
+    switch (D) {
+    case 3: return na_count_fn<3>();
+    case 4: return na_count_fn<4>();
+    case 5: return na_count_fn<5>();
+    case 6: return na_count_fn<6>();
+    case 7: return na_count_fn<7>();
+    case 8: return na_count_fn<8>();
+    case 9: return na_count_fn<9>();
+    case 10: return na_count_fn<10>();
+    default: return nullptr;
+    }
+}
+
+// Set-up, once per device with that device current: the device address of the
+// scratch array (its name in host code is only a stand-in) and the kernels'
+// shared-memory limit.
+int noalloc_setup(unsigned char **scratch)
+{
+    static std::mutex mu;
+    static unsigned char *addr[64] = {};
+    int dev = 0;
+    HWC_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return set_error(HWC_ERR_ARG, "device %d not supported", dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        HWC_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        const int optin = (int)device_smem_optin();
+        for (int D = 3; D <= kMaxD; ++D) {
+            KernelFn fn = na_count_kernel(D);
+            cudaFuncAttributes fa{};
+            HWC_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
+            HWC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              optin - (int)fa.sharedSizeBytes));
+        }
+        addr[dev] = (unsigned char *)p;
+    }
+    *scratch = addr[dev];
+    return HWC_OK;
+}
+
+}  // namespace
+}  // namespace hwc
+
+extern "C" int hwc_count_noalloc(uint32_t g, uint32_t q, const hwc_family_t *fam, uint64_t first,
+                                 uint64_t count, const hwc_tables_t *const *tables, uint64_t max_entries,
+                                 int32_t *counts, uint64_t *mult, uint64_t *n_out, void *stream)
+{
+    using namespace hwc;
+    if (!fam || !tables || !n_out || (max_entries && (!counts || !mult)))
+        return set_error(HWC_ERR_ARG, "null argument");
+    if (g < 1 || g > (uint32_t)kMaxG) return set_error(HWC_ERR_ARG, "g=%u outside [1,%d]", g, kMaxG);
+    const uint32_t d = fam->degree;
+    if (d != 2 * g + 1 && d != 2 * g + 2) return set_error(HWC_ERR_ARG, "degree %u is not 2g+1 or 2g+2", d);
+    if (fam->kind > HWC_FAM_MONIC_NOSUB_SAMPLED) return set_error(HWC_ERR_ARG, "unknown family kind");
+    uint64_t fam_n = 0;
+    int rc = hwc_family_size(q, fam, &fam_n);
+    if (rc) return rc;
+    if (first > fam_n || count > fam_n - first)
+        return set_error(HWC_ERR_RANGE, "members outside the family of %llu", (unsigned long long)fam_n);
+    const uint32_t cap = hash_capacity(g, q, count, 1);
+    if (cap > kNoAllocSlots)
+        return set_error(HWC_ERR_TOO_LARGE, "histogram may need %u hash slots; the fixed scratch has %u", cap,
+                         kNoAllocSlots);
+    // job descriptor from the caller's tables (no table cache, no allocation)
+    KJob kj;
+    std::memset(&kj, 0, sizeof kj);
+    uint32_t p = 0, e = 0;
+    if (!prime_power(q, &p, &e)) return set_error(HWC_ERR_ARG, "q=%u is not an odd prime power", q);
+    kj.g = g;
+    kj.q = q;
+    kj.d = d;
+    kj.kind = fam->kind;
+    kj.p = p;
+    kj.seed = fam->seed;
+    kj.first = first;
+    kj.count = count;
+    kj.fam_mz = 1;
+    for (uint32_t i = 0; i + 1 < d; ++i) kj.fam_mz *= q;
+    kj.qd = kj.fam_mz * q;
+    kj.n_tiles = (count + kTileMembers - 1) / kTileMembers;
+    for (uint32_t k = 1; k <= g; ++k) {
+        const hwc_tables_t *h = tables[k - 1];
+        if (!h || !h->t || h->t->q != q || h->t->k != k)
+            return set_error(HWC_ERR_ARG, "tables[%u] must be the tables of F_%u^%u", k - 1, q, k);
+        const Tables *t = h->t;
+        kj.Q[k - 1] = t->Q;
+        kj.L[k - 1] = t->L;
+        kj.barrett[k - 1] = (uint32_t)((1ull << 32) / t->L);
+        kj.zech2[k - 1] = t->d_zech2;
+        kj.zech3[k - 1] = t->d_zech3;
+        kj.zech2w[k - 1] = t->d_zech2w;
+        kj.coef_log[k - 1] = t->d_coef_log;
+    }
+    layout_job_smem(kj, device_smem_optin() - 4096);
+    unsigned char *scratch = nullptr;
+    if ((rc = noalloc_setup(&scratch))) return rc;
+    unsigned long long *hdr = reinterpret_cast<unsigned long long *>(scratch);
+    kj.stats = hdr;                   // stats[0..3], entries at stats[4]
+    kj.hkeys = hdr + 8;
+    kj.hcounts = hdr + 8 + kNoAllocSlots;
+    kj.hmask = cap - 1;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int sms = device_sm_count();
+    k_na_clear<<<sms, 256, 0, s>>>(scratch, cap);
+    HWC_CUDA_TRY(cudaGetLastError());
+    if (count) {
+        int ctas = 0;
+        KernelFn fn = na_count_kernel((int)d);
+        HWC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctas, fn, 256, kj.smem_bytes));
+        if (ctas <= 0) return set_error(HWC_ERR_TOO_LARGE, "no CTA fits %u bytes of shared memory", kj.smem_bytes);
+        const uint64_t need = (kj.n_tiles + 7) / 8;
+        const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)sms * ctas));
+        void *args[] = {(void *)&kj};
+        HWC_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(256), args, kj.smem_bytes, s));
+    }
+    k_na_emit<<<sms, 256, 0, s>>>(kj, counts, mult, max_entries);
+    HWC_CUDA_TRY(cudaGetLastError());
+    k_na_finish<<<1, 32, 0, s>>>(kj, n_out);
+    HWC_CUDA_TRY(cudaGetLastError());
+    unsigned long long st[5] = {};
+    HWC_CUDA_TRY(cudaMemcpyAsync(st, kj.stats, sizeof st, cudaMemcpyDeviceToHost, s));
+    HWC_CUDA_TRY(cudaStreamSynchronize(s));
+    if (st[2]) return set_error(HWC_ERR_TOO_LARGE, "histogram hash overflowed");
+    if (st[4] > max_entries)
+        return set_error(HWC_ERR_TOO_LARGE, "%llu histogram entries, output holds %llu",
+                         (unsigned long long)st[4], (unsigned long long)max_entries);
+    return HWC_OK;
+}

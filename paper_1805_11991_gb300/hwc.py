@@ -97,6 +97,7 @@ def load(build_if_missing: bool = True):
             "hwc_serve_latency": (c_int, [vp, u64, P(ctypes.c_double), P(ctypes.c_double)]),
             "hwc_serve_close": (c_int, [vp]),
             "hwc_probe_smem_gather": (c_int, [u32, u32, P(ctypes.c_double)]),
+            "hwc_count_noalloc": (c_int, [u32, u32, P(Family), u64, u64, P(vp), u64, vp, vp, vp, vp]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(lib, name)
@@ -293,6 +294,18 @@ def batch_run(jobs, flags: int = 0, stream=None):
     outs = (ctypes.c_void_p * len(jobs))()
     _check(lib.hwc_batch_run(arr, len(jobs), flags, _stream_ptr(stream), outs))
     return [_take_hist(ctypes.c_void_p(o)) for o in outs]
+
+
+def count_noalloc(g: int, q: int, fam: Family, first: int, n: int, tables, max_entries: int,
+                  d_counts: int, d_mult: int, d_n_out: int, stream=None) -> None:
+    """hwc_count_noalloc: the library allocates nothing; `tables` are the g
+    Tables objects of F_{q^k}, k = 1..g, and d_counts / d_mult / d_n_out are
+    DEVICE pointers (int32 [max_entries*g], uint64 [max_entries], uint64 [3])
+    the caller owns."""
+    load()
+    handles = (ctypes.c_void_p * len(tables))(*[t._h.value for t in tables])
+    _check(_lib.hwc_count_noalloc(g, q, ctypes.byref(fam), first, n, handles, max_entries,
+                                  d_counts, d_mult, d_n_out, _stream_ptr(stream)))
 
 
 def probe_smem_gather(entries: int, iters: int = 4096) -> float:
