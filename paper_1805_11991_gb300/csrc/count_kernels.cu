@@ -1,28 +1,7 @@
-// count_kernels.cu -- the point-counting hot path on sm_103a.
-//
-// One warp handles a tile of 32 consecutive members of a family:
-//   1. each lane decodes one member index into coefficient digits (Algorithm 1
-//      line 3) and tests it for square-freeness by Euclid's algorithm on
-//      gcd(f, f') in Zech arithmetic over F_q;
-//   2. for every square-free member of the tile (uniform loop) and every
-//      k = 1..g the 32 lanes sweep x = alpha^j over F_Q^x (lines 6-14), two
-//      x per lane per step, evaluating f by Horner's rule in the log domain
-//      with one Zech lookup per nonzero coefficient (eq. 2.1, 3.1-3.2), and
-//      sum chi(f(x)) = (-1)^log (the parity of the log, L being even);
-//   3. #C_k = Q + sum_x chi(f(x)) + 1 + chi(f(inf)) (Sec. 1.1), i.e.
-//      r^0 + 2 r^sq + 1 + chi(f(inf)); the lanes' tuples are aggregated
-//      within the warp (match.any) and added into an open-addressing hash
-//      in global memory (line 21, weight 1).
-//
-// The Horner chain is kept in "Zech index" form.  With lambda_i = log c_i and
-// the nonzero coefficients below the lead at i_1 > i_2 > ..., the partial
-// value after c_{i_t} is alpha^(lambda_{i_t} + Z(u_t)) and
-//     u_{t+1} = Z(u_t) + (lambda_{i_t} - lambda_{i_{t+1}} + (i_t - i_{t+1}) j)  (mod L),
-// so each step is one table read and a few integer adds.  The table is read
-// through a doubled layout T[u] = Z(u mod L), u in [0, 2L), so u needs no
-// reduction; the entry with 1 + alpha^u = 0 holds the poison value 2L, and
-// T[2L] = 2L, so a vanishing partial sum (probability ~ 1/Q per step, Sec. 4)
-// makes the chain stick at 2L; such lanes are redone by a branchy Horner.
+// count_kernels.cu -- launch wrappers of the count kernels, the histogram
+// clear/compaction kernels, and the allocation-free entry point.  The
+// per-member Horner kernels are in horner.cuh (instantiated in horner_*.cu),
+// the c_0 fan-out kernels in fanout.cuh (fanout_*.cu).
 #include "count_common.cuh"
 
 #include <algorithm>
@@ -30,261 +9,6 @@
 
 namespace hwc {
 namespace {
-
-template <int D, int I1, bool TRIPLE, class Tab>
-__device__ __forceinline__ void dense_chain(const Tab T, const uint32_t (&dli)[D], uint32_t L,
-                                            uint32_t cap, uint32_t xA, uint32_t xB,
-                                            uint32_t &uA, uint32_t &uB)
-{
-#pragma unroll
-    for (int i = I1 - 1; i >= 0; --i) {
-        const uint32_t zA = T[uA], zB = T[uB];
-        uA = chain_step<TRIPLE>(zA, dli[i], xA, L, cap);
-        uB = chain_step<TRIPLE>(zB, dli[i], xB, L, cap);
-    }
-}
-
-template <int D, bool TRIPLE, class Tab>
-__device__ __forceinline__ int field_chi_sum(const Tab T, uint32_t L, uint32_t bar,
-                                             const uint32_t (&lam)[D + 1], uint32_t nz, int lane)
-{
-    const uint32_t cap = TRIPLE ? 3 * L : 2 * L;
-    int S = 0;
-    if (nz == 0) {   // f = c_D x^D
-        for (uint32_t j = lane; j < L; j += 32) S += ((lam[D] + (uint32_t)D * j) & 1u) ? -1 : 1;
-        return S;
-    }
-    const int i1 = 31 - __clz(nz);
-    const int is = __ffs(nz) - 1;
-    const uint32_t g1 = (uint32_t)(D - i1);
-    // first step index: lam_D + g1*j - lam_{i1}, kept in [0, 2L)
-    const uint32_t base1 = lam[D] + (L - lam[i1]);     // < 2L
-    const uint32_t lam_last = lam[is];
-    const uint32_t is_odd = (uint32_t)is & 1u;
-    // per-position constants of the chain (static indices: registers)
-    uint32_t dli[D], gpi[D];
-    {
-        uint32_t lp = lam[i1];
-        int ip = i1;
-#pragma unroll
-        for (int i = D - 1; i >= 0; --i) {
-            dli[i] = 0;
-            gpi[i] = 0;
-            if (i < i1 && ((nz >> i) & 1u)) {
-                dli[i] = addmod(lp, L - lam[i], L);
-                gpi[i] = (uint32_t)(ip - i);
-                lp = lam[i];
-                ip = i;
-            }
-        }
-    }
-    // dense patterns get a branch-free chain
-    const int dense = (nz == (1u << (D - 1)) - 1u) ? 2 : (nz == (1u << D) - 1u) ? 1 : 0;
-    for (uint32_t j0 = 0; j0 < L; j0 += 64) {
-        const uint32_t jA = j0 + lane, jB = j0 + 32 + lane;
-        const bool vA = jA < L, vB = jB < L;
-        const uint32_t xA = vA ? jA : 0, xB = vB ? jB : 0;
-        uint32_t mA, mB;
-        if (g1 == 2) {   // lead at D, first nonzero at D-2: 2j mod L
-            mA = min(2 * xA, 2 * xA - L);
-            mB = min(2 * xB, 2 * xB - L);
-        } else {
-            mA = mulmod_small(g1, xA, L, bar);
-            mB = mulmod_small(g1, xB, L, bar);
-        }
-        uint32_t uA = base1 + mA, uB = base1 + mB;       // < 3L
-        if (!TRIPLE) {
-            uA = min(uA, uA - L);                          // unsigned: back below 2L
-            uB = min(uB, uB - L);
-        }
-        if (dense == 2) {
-            dense_chain<D, D - 2, TRIPLE>(T, dli, L, cap, xA, xB, uA, uB);
-        } else if (dense == 1) {
-            dense_chain<D, D - 1, TRIPLE>(T, dli, L, cap, xA, xB, uA, uB);
-        } else {
-#pragma unroll
-            for (int i = D - 2; i >= 0; --i) {
-                if (gpi[i] == 0) continue;                 // zero coefficient or above i1
-                uint32_t sA, sB;
-                if (gpi[i] == 1) {
-                    sA = xA;
-                    sB = xB;
-                } else {
-                    sA = mulmod_small(gpi[i], xA, L, bar);
-                    sB = mulmod_small(gpi[i], xB, L, bar);
-                }
-                const uint32_t zA = T[uA], zB = T[uB];
-                uA = chain_step<TRIPLE>(zA, dli[i], sA, L, cap);
-                uB = chain_step<TRIPLE>(zB, dli[i], sB, L, cap);
-            }
-        }
-        const uint32_t zA = T[uA], zB = T[uB];
-        // f(x) = alpha^(lam_last + z + is*j): chi is the parity of the exponent
-        int cA = 1 - 2 * (int)((lam_last ^ zA ^ (xA & is_odd)) & 1u);
-        int cB = 1 - 2 * (int)((lam_last ^ zB ^ (xB & is_odd)) & 1u);
-        const bool pA = vA && zA >= cap, pB = vB && zB >= cap;
-        if (__any_sync(kFull, pA || pB)) {
-            if (pA) cA = slow_chi<D>(T, L, cap, lam, nz, xA);
-            if (pB) cB = slow_chi<D>(T, L, cap, lam, nz, xB);
-        }
-        S += (vA ? cA : 0) + (vB ? cB : 0);
-    }
-    return S;
-}
-
-// ---------------------------------------------------------------------
-// one tile of 32 members, processed by one warp
-
-template <int D>
-__device__ void process_tile(const KJob &J, uint64_t tile, const uint8_t *smem, int lane,
-                             WarpStats &st)
-{
-    constexpr int G = (D - 1) / 2;
-    const uint64_t m = tile * kTileMembers + lane;
-    const bool valid = m < J.count;
-    uint32_t c[D + 1];
-#pragma unroll
-    for (int i = 0; i <= D; ++i) c[i] = 0;
-    c[D] = 1;
-    if (valid) decode_member<D>(J, m, c);
-
-    const uint16_t *s16 = reinterpret_cast<const uint16_t *>(smem);
-    const uint32_t *s32 = reinterpret_cast<const uint32_t *>(smem);
-
-    bool sqf = false;
-    if (valid) {
-        const uint32_t *coef1 = s32 + J.coef_off[0];
-        if (J.tab_kind[0] != kTabDoubleGlobal) {
-            FqLog<TabS> F{TabS{s16 + J.tab_off[0]}, J.L[0]};
-            sqf = squarefree<D>(F, coef1, J.p, c);
-        } else {
-            FqLog<TabG> F{TabG{J.zech2w[0]}, J.L[0]};
-            sqf = squarefree<D>(F, coef1, J.p, c);
-        }
-    }
-    const unsigned vmask = __ballot_sync(kFull, valid);
-    const unsigned smask = __ballot_sync(kFull, sqf);
-    if (lane == 0) {
-        st.examined += __popc(vmask);
-        st.sqf += __popc(smask);
-    }
-    unsigned todo = J.unfiltered ? vmask : smask;
-
-    int32_t myN[G];
-#pragma unroll
-    for (int k = 0; k < G; ++k) myN[k] = 0;
-
-    while (todo) {
-        const int src = __ffs(todo) - 1;
-        todo &= todo - 1;
-        uint32_t cc[D + 1];
-#pragma unroll
-        for (int i = 0; i <= D; ++i) cc[i] = __shfl_sync(kFull, c[i], src);
-        uint32_t nz = 0;
-#pragma unroll
-        for (int i = 0; i < D; ++i) nz |= (cc[i] != 0 ? 1u : 0u) << i;
-#pragma unroll
-        for (int k = 0; k < G; ++k) {
-            const uint32_t L = J.L[k];
-            const uint32_t *coefk = s32 + J.coef_off[k];
-            uint32_t lam[D + 1];
-#pragma unroll
-            for (int i = 0; i <= D; ++i) lam[i] = coefk[cc[i]];
-            int S;
-            const uint32_t kind = J.tab_kind[k];
-            if (kind == kTabTripleSmem)
-                S = field_chi_sum<D, true>(TabS{s16 + J.tab_off[k]}, L, J.barrett[k], lam, nz, lane);
-            else if (kind == kTabDoubleSmem)
-                S = field_chi_sum<D, false>(TabS{s16 + J.tab_off[k]}, L, J.barrett[k], lam, nz, lane);
-            else
-                S = field_chi_sum<D, false>(TabG{J.zech2w[k]}, L, J.barrett[k], lam, nz, lane);
-            if (lane == 0 && cc[0] != 0) S += (lam[0] & 1u) ? -1 : 1;   // x = 0
-            S = __reduce_add_sync(kFull, S);
-            // points at infinity: 1 + chi(c_{2g+2})
-            int inf = 1;
-            if (D == 2 * G + 2) inf += (lam[D] & 1u) ? -1 : 1;
-            if (lane == src) myN[k] = (int32_t)J.Q[k] + S + inf;
-        }
-    }
-
-    if (J.member_counts) {
-        if (valid) {
-#pragma unroll
-            for (int k = 0; k < G; ++k) J.member_counts[m * G + k] = (sqf || J.unfiltered) ? myN[k] : 0;
-            J.member_sqf[m] = sqf ? 1 : 0;
-        }
-        return;
-    }
-    unsigned long long key = 0;
-#pragma unroll
-    for (int k = 0; k < G; ++k) {
-        const int a = (int)J.Q[k] + 1 - myN[k];   // eq. 1.1
-        key |= (unsigned long long)((uint32_t)(a + 32768) & 0xFFFFu) << (16 * k);
-    }
-    if (sqf) {
-        const unsigned peers = __match_any_sync(smask, key);
-        if (lane == __ffs(peers) - 1) hist_insert(J, key, __popc(peers));
-    }
-}
-
-// ---------------------------------------------------------------------
-// kernels
-
-template <int D>
-__global__ void __launch_bounds__(256) k_plain(const KJob *__restrict__ jp)
-{
-    extern __shared__ __align__(16) uint8_t smem[];
-    const KJob &J = *jp;
-    stage_job(J, smem);
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    WarpStats st;
-    for (uint64_t t = (uint64_t)blockIdx.x * nw + warp; t < J.n_tiles; t += (uint64_t)gridDim.x * nw)
-        process_tile<D>(J, t, smem, lane, st);
-    flush_stats(J, st, lane);
-}
-
-// Persistent: CTAs pull work items (a run of tiles of one job) from a counter
-// until the queue is empty; a CTA restages tables only when its job changes.
-template <int D>
-__global__ void __launch_bounds__(256) k_persistent(const KJob *__restrict__ jobs,
-                                                    const uint64_t *__restrict__ item_start,
-                                                    uint32_t n_jobs, uint64_t n_items,
-                                                    unsigned long long *counter, uint32_t item_tiles)
-{
-    extern __shared__ __align__(16) uint8_t smem[];
-    __shared__ unsigned long long s_item;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int cur = -1;
-    WarpStats st;
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1ull);
-        __syncthreads();
-        const uint64_t item = s_item;
-        __syncthreads();   // everyone has read s_item
-        if (item >= n_items) break;
-        // job owning this item: item_start is ascending, item_start[n_jobs] = n_items
-        uint32_t lo = 0, hi = n_jobs;
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (item_start[mid] <= item) lo = mid;
-            else hi = mid;
-        }
-        const int jb = (int)lo;
-        if (jb != cur) {
-            if (cur >= 0) flush_stats(jobs[cur], st, lane);
-            stage_job(jobs[jb], smem);
-            __syncthreads();
-            cur = jb;
-        }
-        const KJob &J = jobs[jb];
-        const uint64_t t0 = (item - item_start[jb]) * item_tiles;
-        const uint64_t t1 = min(t0 + item_tiles, J.n_tiles);
-        for (uint64_t t = t0 + warp; t < t1; t += nw) process_tile<D>(J, t, smem, lane, st);
-        __syncthreads();   // tables may be restaged next iteration
-    }
-    if (cur >= 0) flush_stats(jobs[cur], st, lane);
-}
 
 __global__ void k_clear(const KJob *__restrict__ jobs, uint32_t n_jobs, unsigned long long *counters,
                         uint32_t n_counters)
@@ -338,34 +62,33 @@ __global__ void k_compact(const KJob *__restrict__ jobs, uint32_t n_jobs)
 
 using KernelFn = const void *;
 
-static KernelFn plain_fn(int D)
+KernelFn horner_kernel(int D, int which)
 {
+    return D <= 6 ? horner_kernel_a(D, which) : D <= 8 ? horner_kernel_b(D, which) : horner_kernel_c(D, which);
+}
+
+KernelFn fan_kernel(int D, int W, bool persistent)
+{
+    if (W != 1 && W != 2) return nullptr;
     switch (D) {
-    case 3: return (KernelFn)k_plain<3>;
-    case 4: return (KernelFn)k_plain<4>;
-    case 5: return (KernelFn)k_plain<5>;
-    case 6: return (KernelFn)k_plain<6>;
-    case 7: return (KernelFn)k_plain<7>;
-    case 8: return (KernelFn)k_plain<8>;
-    case 9: return (KernelFn)k_plain<9>;
-    case 10: return (KernelFn)k_plain<10>;
+    case 3: case 4: return fan_kernel_a(D, W, persistent);
+    case 5: return fan_kernel_b(D, W, persistent);
+    case 6: return fan_kernel_c(D, W, persistent);
+    case 7: return fan_kernel_d(D, W, persistent);
+    case 8: return fan_kernel_f(D, W, persistent);
+    case 9: case 10: return fan_kernel_e(D, W, persistent);
     default: return nullptr;
     }
 }
 
+static KernelFn plain_fn(int D)
+{
+    return horner_kernel(D, 0);
+}
+
 static KernelFn persistent_fn(int D)
 {
-    switch (D) {
-    case 3: return (KernelFn)k_persistent<3>;
-    case 4: return (KernelFn)k_persistent<4>;
-    case 5: return (KernelFn)k_persistent<5>;
-    case 6: return (KernelFn)k_persistent<6>;
-    case 7: return (KernelFn)k_persistent<7>;
-    case 8: return (KernelFn)k_persistent<8>;
-    case 9: return (KernelFn)k_persistent<9>;
-    case 10: return (KernelFn)k_persistent<10>;
-    default: return nullptr;
-    }
+    return horner_kernel(D, 1);
 }
 
 int prepare_count_kernels(void)
@@ -380,6 +103,7 @@ int prepare_count_kernels(void)
     for (int D = 3; D <= kMaxD; ++D) {
         for (KernelFn fn : {plain_fn(D), persistent_fn(D), fan_kernel(D, 1, false), fan_kernel(D, 1, true),
                             fan_kernel(D, 2, false), fan_kernel(D, 2, true)}) {
+            if (!fn) continue;   // no kernel for this degree and row width
             cudaFuncAttributes fa{};
             HWC_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));   // static smem counts against the limit
             HWC_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -505,19 +229,6 @@ __global__ void k_na_clear(unsigned char *scratch, uint32_t slots)
     }
 }
 
-template <int D>
-__global__ void __launch_bounds__(256) k_na_count(const KJob J)
-{
-    extern __shared__ __align__(16) uint8_t smem[];
-    stage_job(J, smem);
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    WarpStats st;
-    for (uint64_t t = (uint64_t)blockIdx.x * nw + warp; t < J.n_tiles; t += (uint64_t)gridDim.x * nw)
-        process_tile<D>(J, t, smem, lane, st);
-    flush_stats(J, st, lane);
-}
-
 // filled hash slots -> caller's (#C_1..#C_g, multiplicity) arrays, hash order
 __global__ void k_na_emit(const KJob J, int32_t *counts, uint64_t *mult, uint64_t max_entries)
 {
@@ -545,25 +256,9 @@ __global__ void k_na_finish(const KJob J, uint64_t *n_out)
     }
 }
 
-template <int D>
-KernelFn na_count_fn()
-{
-    return (KernelFn)k_na_count<D>;
-}
-
 KernelFn na_count_kernel(int D)
 {
-    switch (D) {
-    case 3: return na_count_fn<3>();
-    case 4: return na_count_fn<4>();
-    case 5: return na_count_fn<5>();
-    case 6: return na_count_fn<6>();
-    case 7: return na_count_fn<7>();
-    case 8: return na_count_fn<8>();
-    case 9: return na_count_fn<9>();
-    case 10: return na_count_fn<10>();
-    default: return nullptr;
-    }
+    return horner_kernel(D, 2);
 }
 
 // Set-up, once per device with that device current: the device address of the

@@ -1,4 +1,5 @@
-// fanout_kernels.cu -- c_0 fan-out count kernel for enumerated families.
+// fanout.cuh -- c_0 fan-out count kernel for enumerated families; instantiated
+// per degree in fanout_a.cu .. fanout_e.cu.
 //
 // Consecutive members of a family differ first in c_0 (digit 0 of the member
 // index), so q consecutive members f_c = g + c (c in F_q) share
@@ -16,6 +17,7 @@
 //     #C_k(f_c) = Q + sum_x chi(f_c(x)) + 1 + chi(f(inf))          (Sec. 1.1).
 // Members are counted exactly as in Algorithm 1 lines 7-14; only the work
 // shared by the q members of a group is done once.
+#pragma once
 #include "count_common.cuh"
 
 #include <algorithm>
@@ -45,10 +47,16 @@ struct Planes {
 
 // Horner in the log domain for h(x) = sum_{i>=1} c_i x^(i-1) with explicit
 // zero handling; returns log h(x) or L when h(x) = 0.
+template <int D>
+struct LamV {
+    uint32_t v[D + 1];
+};
+
 template <int D, class Tab>
-__device__ __forceinline__ uint32_t slow_log_h(const Tab T, uint32_t L, uint32_t cap,
-                                               const uint32_t (&lam)[D + 1], uint32_t nz, uint32_t j)
+__device__ __noinline__ uint32_t slow_log_h(const Tab T, uint32_t L, uint32_t cap, const LamV<D> lamv,
+                                            uint32_t nz, uint32_t j)
 {
+    const uint32_t(&lam)[D + 1] = lamv.v;
     uint32_t l = lam[D];
     bool zero = false;
 #pragma unroll
@@ -110,6 +118,30 @@ __device__ __forceinline__ void make_hchain(HChain<D> &H, const uint32_t (&lam)[
     H.dense = (nzh == full2) ? 2 : 0;
 }
 
+// chain steps for coefficient patterns with zeros below the lead (any gaps);
+// out of line: such groups are a few percent of a family
+template <int D, bool TRIPLE, class Tab>
+__device__ __noinline__ void general_chain(const Tab T, uint32_t L, uint32_t bar, uint32_t cap,
+                                           const HChain<D> H, uint32_t xA, uint32_t xB, uint32_t &uA,
+                                           uint32_t &uB)
+{
+#pragma unroll
+    for (int i = D - 2; i >= 1; --i) {
+        if (H.gpi[i] == 0) continue;
+        uint32_t sA, sB;
+        if (H.gpi[i] == 1) {
+            sA = xA;
+            sB = xB;
+        } else {
+            sA = mulmod_small(H.gpi[i], xA, L, bar);
+            sB = mulmod_small(H.gpi[i], xB, L, bar);
+        }
+        const uint32_t zA = T[uA], zB = T[uB];
+        uA = chain_step<TRIPLE>(zA, H.dli[i], sA, L, cap);
+        uB = chain_step<TRIPLE>(zB, H.dli[i], sB, L, cap);
+    }
+}
+
 // log y for x = alpha^j (y = x h(x)), or L when y = 0; two x per lane.
 template <int D, bool TRIPLE, class Tab>
 __device__ __forceinline__ void log_y_pair(const Tab T, uint32_t L, uint32_t bar, const HChain<D> &H,
@@ -143,21 +175,7 @@ __device__ __forceinline__ void log_y_pair(const Tab T, uint32_t L, uint32_t bar
             uB = chain_step<TRIPLE>(zB, H.dli[i], xB, L, cap);
         }
     } else {
-#pragma unroll
-        for (int i = D - 2; i >= 1; --i) {
-            if (H.gpi[i] == 0) continue;
-            uint32_t sA, sB;
-            if (H.gpi[i] == 1) {
-                sA = xA;
-                sB = xB;
-            } else {
-                sA = mulmod_small(H.gpi[i], xA, L, bar);
-                sB = mulmod_small(H.gpi[i], xB, L, bar);
-            }
-            const uint32_t zA = T[uA], zB = T[uB];
-            uA = chain_step<TRIPLE>(zA, H.dli[i], sA, L, cap);
-            uB = chain_step<TRIPLE>(zB, H.dli[i], sB, L, cap);
-        }
+        general_chain<D, TRIPLE>(T, L, bar, cap, H, xA, xB, uA, uB);
     }
     const uint32_t zA = T[uA], zB = T[uB];
     // y = alpha^(lam_last + z + tail*j)
@@ -173,12 +191,15 @@ __device__ __forceinline__ void log_y_pair(const Tab T, uint32_t L, uint32_t bar
     yB = addmod(addmod(H.lam_last, zB, L), tB, L);
     const bool pA = zA >= cap, pB = zB >= cap;
     if (__any_sync(0xFFFFFFFFu, pA || pB)) {
+        LamV<D> lv;
+#pragma unroll
+        for (int i = 0; i <= D; ++i) lv.v[i] = lam[i];
         if (pA) {
-            const uint32_t lh = slow_log_h<D>(T, L, cap, lam, nz, xA);
+            const uint32_t lh = slow_log_h<D>(T, L, cap, lv, nz, xA);
             yA = lh == L ? L : addmod(lh, xA, L);
         }
         if (pB) {
-            const uint32_t lh = slow_log_h<D>(T, L, cap, lam, nz, xB);
+            const uint32_t lh = slow_log_h<D>(T, L, cap, lv, nz, xB);
             yB = lh == L ? L : addmod(lh, xB, L);
         }
     }
@@ -382,14 +403,21 @@ __device__ __forceinline__ void group_field(const Tab T, const KJob &J, int k, c
 #pragma unroll
             for (int w = 0; w < W; ++w) add8(P[w], a[w]);
         }
+        // per-lane counts are below 8 * blocks: fewer planes to add across lanes
+        const uint32_t nblk = (cend - c0 + 255) / 256;
 #pragma unroll
-        for (int w = 0; w < W; ++w) cnt[w] += reduce_planes<8>(P[w].p);
+        for (int w = 0; w < W; ++w) {
+            if (nblk <= 3) cnt[w] += reduce_planes<5>(P[w].p);
+            else if (nblk <= 7) cnt[w] += reduce_planes<6>(P[w].p);
+            else if (nblk <= 15) cnt[w] += reduce_planes<7>(P[w].p);
+            else cnt[w] += reduce_planes<8>(P[w].p);
+        }
     }
 }
 
 // one group of q members (c_0 = 0..q-1) for one warp
 template <int D, int W>
-__device__ void process_group(const KJob &J, uint64_t gtile, const uint8_t *smem, uint32_t *zc, int lane,
+__device__ __noinline__ void process_group(const KJob &J, uint64_t gtile, const uint8_t *smem, uint32_t *zc, int lane,
                               WarpStats &st)
 {
     constexpr int G = (D - 1) / 2;
@@ -570,29 +598,11 @@ __global__ void __launch_bounds__(kFanWarps * 32, fan_min_ctas<D, W>()) k_fan_pe
     if (cur >= 0) flush_stats(jobs[cur], st, lane);
 }
 
-using KernelFn = const void *;
-
-template <int W>
-KernelFn fan_fn_w(int D, bool persistent)
+template <int D, int W>
+const void *fan_pick(bool persistent)
 {
-    switch (D) {
-    case 3: return persistent ? (KernelFn)k_fan_persistent<3, W> : (KernelFn)k_fan_plain<3, W>;
-    case 4: return persistent ? (KernelFn)k_fan_persistent<4, W> : (KernelFn)k_fan_plain<4, W>;
-    case 5: return persistent ? (KernelFn)k_fan_persistent<5, W> : (KernelFn)k_fan_plain<5, W>;
-    case 6: return persistent ? (KernelFn)k_fan_persistent<6, W> : (KernelFn)k_fan_plain<6, W>;
-    case 7: return persistent ? (KernelFn)k_fan_persistent<7, W> : (KernelFn)k_fan_plain<7, W>;
-    case 8: return persistent ? (KernelFn)k_fan_persistent<8, W> : (KernelFn)k_fan_plain<8, W>;
-    case 9: return persistent ? (KernelFn)k_fan_persistent<9, W> : (KernelFn)k_fan_plain<9, W>;
-    case 10: return persistent ? (KernelFn)k_fan_persistent<10, W> : (KernelFn)k_fan_plain<10, W>;
-    default: return nullptr;
-    }
+    return persistent ? (const void *)k_fan_persistent<D, W> : (const void *)k_fan_plain<D, W>;
 }
 
 }  // namespace
-
-KernelFn fan_kernel(int D, int W, bool persistent)
-{
-    return W == 1 ? fan_fn_w<1>(D, persistent) : W == 2 ? fan_fn_w<2>(D, persistent) : nullptr;
-}
-
 }  // namespace hwc

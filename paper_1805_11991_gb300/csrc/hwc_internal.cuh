@@ -154,8 +154,19 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit);
 int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n, uint32_t flags);
 // launch shape for a kernel (degree, method, row words) at this much dynamic smem
 int choose_shape(int D, uint32_t method, uint32_t words, uint32_t smem, bool persistent, LaunchShape *out);
-// fan-out kernels (fanout_kernels.cu)
+// kernel entry points by degree: which = 0 plain, 1 persistent, 2 allocation-free
+const void *horner_kernel(int D, int which);
+const void *horner_kernel_a(int D, int which);   // horner_a.cu, D = 3..6
+const void *horner_kernel_b(int D, int which);   // horner_b.cu, D = 7, 8
+const void *horner_kernel_c(int D, int which);   // horner_c.cu, D = 9, 10
+// c_0 fan-out kernels (fanout.cuh), W = row words
 const void *fan_kernel(int D, int W, bool persistent);
+const void *fan_kernel_a(int D, int W, bool persistent);   // fanout_a.cu, D = 3, 4
+const void *fan_kernel_b(int D, int W, bool persistent);   // fanout_b.cu, D = 5
+const void *fan_kernel_c(int D, int W, bool persistent);   // fanout_c.cu, D = 6
+const void *fan_kernel_d(int D, int W, bool persistent);   // fanout_d.cu, D = 7
+const void *fan_kernel_f(int D, int W, bool persistent);   // fanout_f.cu, D = 8
+const void *fan_kernel_e(int D, int W, bool persistent);   // fanout_e.cu, D = 9, 10
 // hash slots for a job of `count` members (power of two)
 uint32_t hash_capacity(uint32_t g, uint32_t q, uint64_t count, uint32_t scale);
 
