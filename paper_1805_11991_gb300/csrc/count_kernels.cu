@@ -81,11 +81,6 @@ KernelFn fan_kernel(int D, int W, bool persistent)
     }
 }
 
-static KernelFn plain_fn(int D)
-{
-    return horner_kernel(D, 0);
-}
-
 static KernelFn persistent_fn(int D)
 {
     return horner_kernel(D, 1);
@@ -101,8 +96,7 @@ int prepare_count_kernels(void)
     if (dev >= 0 && dev < 64 && done[dev]) return HWC_OK;
     const int optin = (int)device_smem_optin();
     for (int D = 3; D <= kMaxD; ++D) {
-        for (KernelFn fn : {plain_fn(D), persistent_fn(D), fan_kernel(D, 1, false), fan_kernel(D, 1, true),
-                            fan_kernel(D, 2, false), fan_kernel(D, 2, true)}) {
+        for (KernelFn fn : {persistent_fn(D), fan_kernel(D, 1, true), fan_kernel(D, 2, true)}) {
             if (!fn) continue;   // no kernel for this degree and row width
             cudaFuncAttributes fa{};
             HWC_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));   // static smem counts against the limit
@@ -133,14 +127,15 @@ uint32_t device_smem_optin(void)
 static KernelFn kernel_for(int D, uint32_t method, uint32_t words, bool persistent)
 {
     if (method == 1) return fan_kernel(D, (int)words, persistent);
-    return persistent ? persistent_fn(D) : plain_fn(D);
+    (void)persistent;   // every run is a persistent launch (a plain run has one job per launch)
+    return persistent_fn(D);
 }
 
 int max_ctas_per_sm(int D, uint32_t method, uint32_t words, int block, uint32_t smem_bytes,
                     bool persistent, int *out)
 {
     int n = 0;
-    KernelFn fn = kernel_for(D, method, words, persistent);
+    KernelFn fn = kernel_for(D, method, words, true);
     if (!fn) return set_error(HWC_ERR_ARG, "degree %d has no kernel", D);
     HWC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, smem_bytes));
     *out = n;
@@ -153,19 +148,6 @@ int launch_clear(const KJob *d_jobs, uint32_t n_jobs, unsigned long long *d_coun
     dim3 grid(device_sm_count(), std::max<uint32_t>(n_jobs, 1));
     k_clear<<<grid, 256, 0, s>>>(d_jobs, n_jobs, d_counters, n_counters);
     HWC_CUDA_TRY(cudaGetLastError());
-    return HWC_OK;
-}
-
-int launch_plain(const KJob *d_job, const KJob &h_job, const LaunchShape &sh, cudaStream_t s)
-{
-    int grid = sh.grid;
-    if (grid <= 0) grid = device_sm_count();
-    const uint64_t need = (h_job.n_tiles + (sh.block / 32) - 1) / (sh.block / 32);
-    if ((uint64_t)grid > need) grid = (int)std::max<uint64_t>(need, 1);
-    KernelFn fn = kernel_for((int)h_job.d, h_job.method, h_job.words, false);
-    if (!fn) return set_error(HWC_ERR_ARG, "degree %u has no kernel", h_job.d);
-    void *args[] = {(void *)&d_job};
-    HWC_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(sh.block), args, h_job.smem_bytes, s));
     return HWC_OK;
 }
 

@@ -417,7 +417,7 @@ __device__ __forceinline__ void group_field(const Tab T, const KJob &J, int k, c
 
 // one group of q members (c_0 = 0..q-1) for one warp
 template <int D, int W>
-__device__ __noinline__ void process_group(const KJob &J, uint64_t gtile, const uint8_t *smem, uint32_t *zc, int lane,
+__device__ __forceinline__ void process_group(const KJob &J, uint64_t gtile, const uint8_t *smem, uint32_t *zc, int lane,
                               WarpStats &st)
 {
     constexpr int G = (D - 1) / 2;
@@ -543,21 +543,6 @@ __device__ __noinline__ void process_group(const KJob &J, uint64_t gtile, const 
 }
 
 template <int D, int W>
-__global__ void __launch_bounds__(kFanWarps * 32, fan_min_ctas<D, W>()) k_fan_plain(const KJob *__restrict__ jp)
-{
-    extern __shared__ __align__(16) uint8_t smem[];
-    __shared__ uint32_t zc_all[kFanWarps][64];
-    const KJob &J = *jp;
-    stage_job(J, smem);
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    WarpStats st;
-    for (uint64_t t = (uint64_t)blockIdx.x * nw + warp; t < J.n_tiles; t += (uint64_t)gridDim.x * nw)
-        process_group<D, W>(J, t, smem, zc_all[warp], lane, st);
-    flush_stats(J, st, lane);
-}
-
-template <int D, int W>
 __global__ void __launch_bounds__(kFanWarps * 32, fan_min_ctas<D, W>()) k_fan_persistent(const KJob *__restrict__ jobs,
                                                                    const uint64_t *__restrict__ item_start,
                                                                    uint32_t n_jobs, uint64_t n_items,
@@ -601,7 +586,7 @@ __global__ void __launch_bounds__(kFanWarps * 32, fan_min_ctas<D, W>()) k_fan_pe
 template <int D, int W>
 const void *fan_pick(bool persistent)
 {
-    return persistent ? (const void *)k_fan_persistent<D, W> : (const void *)k_fan_plain<D, W>;
+    return persistent ? (const void *)k_fan_persistent<D, W> : nullptr;
 }
 
 }  // namespace

@@ -137,7 +137,7 @@ __device__ __forceinline__ int field_chi_sum(const Tab T, uint32_t L, uint32_t b
 // one tile of 32 members, processed by one warp
 
 template <int D>
-__device__ __noinline__ void process_tile(const KJob &J, uint64_t tile, const uint8_t *smem, int lane,
+__device__ __forceinline__ void process_tile(const KJob &J, uint64_t tile, const uint8_t *smem, int lane,
                              WarpStats &st)
 {
     constexpr int G = (D - 1) / 2;
@@ -231,20 +231,6 @@ __device__ __noinline__ void process_tile(const KJob &J, uint64_t tile, const ui
 // ---------------------------------------------------------------------
 // kernels
 
-template <int D>
-__global__ void __launch_bounds__(256) k_plain(const KJob *__restrict__ jp)
-{
-    extern __shared__ __align__(16) uint8_t smem[];
-    const KJob &J = *jp;
-    stage_job(J, smem);
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    WarpStats st;
-    for (uint64_t t = (uint64_t)blockIdx.x * nw + warp; t < J.n_tiles; t += (uint64_t)gridDim.x * nw)
-        process_tile<D>(J, t, smem, lane, st);
-    flush_stats(J, st, lane);
-}
-
 // Persistent: CTAs pull work items (a run of tiles of one job) from a counter
 // until the queue is empty; a CTA restages tables only when its job changes.
 template <int D>
@@ -303,8 +289,8 @@ __global__ void __launch_bounds__(256) k_na_count(const KJob J)
 template <int D>
 const void *horner_pick(int which)
 {
-    if (which == 0) return (const void *)k_plain<D>;
     if (which == 1) return (const void *)k_persistent<D>;
+    if (which == 0) return nullptr;   // plain runs use the persistent kernel, one job per launch
     return (const void *)k_na_count<D>;
 }
 

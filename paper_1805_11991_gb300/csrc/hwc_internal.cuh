@@ -134,7 +134,6 @@ struct LaunchShape {
 };
 int launch_clear(const KJob *d_jobs, uint32_t n_jobs, unsigned long long *d_counters,
                  uint32_t n_counters, cudaStream_t s);
-int launch_plain(const KJob *d_job, const KJob &h_job, const LaunchShape &sh, cudaStream_t s);
 // one persistent launch over jobs of one degree, method and row width
 int launch_persistent(int D, uint32_t method, uint32_t words, const KJob *d_jobs,
                       const uint64_t *d_item_start, uint32_t n_jobs, uint64_t n_items,
@@ -154,7 +153,7 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit);
 int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n, uint32_t flags);
 // launch shape for a kernel (degree, method, row words) at this much dynamic smem
 int choose_shape(int D, uint32_t method, uint32_t words, uint32_t smem, bool persistent, LaunchShape *out);
-// kernel entry points by degree: which = 0 plain, 1 persistent, 2 allocation-free
+// kernel entry points by degree: which = 1 persistent, 2 allocation-free
 const void *horner_kernel(int D, int which);
 const void *horner_kernel_a(int D, int which);   // horner_a.cu, D = 3..6
 const void *horner_kernel_b(int D, int which);   // horner_b.cu, D = 7, 8

@@ -375,19 +375,11 @@ static int batch_enqueue(hwc_batch *b, cudaStream_t s, bool capturing)
     // inside a graph capture an event record must be an external node to time anything
     if (b->t0) HWC_CUDA_TRY(capturing ? cudaEventRecordWithFlags(b->t0, s, cudaEventRecordExternal)
                                       : cudaEventRecord(b->t0, s));
-    if (b->flags & HWC_FLAG_PLAIN) {
-        for (const BatchGroup &G : b->groups)
-            for (uint32_t i = G.first; i < G.first + G.n; ++i) {
-                rc = launch_plain(b->d_jobs + i, b->jobs[i].kj, G.shape, s);
-                if (rc) return rc;
-            }
-    } else {
-        for (size_t g = 0; g < b->groups.size(); ++g) {
-            const BatchGroup &G = b->groups[g];
-            rc = launch_persistent(G.D, G.method, G.words, b->d_jobs + G.first, b->d_item_start + G.start_off,
-                                   G.n, G.n_items, b->d_counters + g, G.max_smem, G.shape, s);
-            if (rc) return rc;
-        }
+    for (size_t g = 0; g < b->groups.size(); ++g) {
+        const BatchGroup &G = b->groups[g];
+        rc = launch_persistent(G.D, G.method, G.words, b->d_jobs + G.first, b->d_item_start + G.start_off, G.n,
+                               G.n_items, b->d_counters + g, G.max_smem, G.shape, s);
+        if (rc) return rc;
     }
     if (b->t1) HWC_CUDA_TRY(capturing ? cudaEventRecordWithFlags(b->t1, s, cudaEventRecordExternal)
                                       : cudaEventRecord(b->t1, s));
@@ -462,8 +454,9 @@ static int batch_create_impl(const hwc_job_t *jobs, size_t n, uint32_t flags, ui
             batch_release(b);
             return rc;
         }
-        if (b->groups.empty() || b->groups.back().D != (int)kj.d || b->groups.back().method != kj.method ||
-            b->groups.back().words != kj.words) {
+        // plain runs: every job is a group of its own (one launch per job)
+        if (b->groups.empty() || (flags & HWC_FLAG_PLAIN) || b->groups.back().D != (int)kj.d ||
+            b->groups.back().method != kj.method || b->groups.back().words != kj.words) {
             BatchGroup G;
             G.D = (int)kj.d;
             G.method = kj.method;
@@ -512,7 +505,7 @@ static int batch_create_impl(const hwc_job_t *jobs, size_t n, uint32_t flags, ui
             return set_error(HWC_ERR_CUDA, "cudaEventCreate failed");
         }
     }
-    b->launches_per_run = 2 + (uint32_t)(persistent ? b->groups.size() : n);
+    b->launches_per_run = 2 + (uint32_t)b->groups.size();
     if (cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess) {
         batch_release(b);
         return set_error(HWC_ERR_CUDA, "cudaEventCreate failed");
@@ -697,20 +690,31 @@ extern "C" int hwc_count_members(uint32_t g, uint32_t q, const hwc_family_t *fam
     kj.unfiltered = unfiltered ? 1u : 0u;
     cudaStream_t s = (cudaStream_t)stream;
     hwc_batch *b = new hwc_batch();   // allocation holder only
-    if ((rc = dalloc(b, &kj.member_counts, count * g)) || (rc = dalloc(b, &kj.member_sqf, count)) ||
-        (rc = dalloc(b, &kj.stats, 4)) || (rc = dalloc(b, &b->d_jobs, 1))) {
+    LaunchShape sh;
+    rc = choose_shape((int)kj.d, kj.method, kj.words, kj.smem_bytes, true, &sh);
+    uint64_t starts[2] = {0, 0};
+    starts[1] = (kj.n_tiles + sh.item_tiles - 1) / sh.item_tiles;
+    if (rc == HWC_OK &&
+        ((rc = dalloc(b, &kj.member_counts, count * g)) || (rc = dalloc(b, &kj.member_sqf, count)) ||
+         (rc = dalloc(b, &kj.stats, 4)) || (rc = dalloc(b, &b->d_jobs, 1)) ||
+         (rc = dalloc(b, &b->d_item_start, 2)) || (rc = dalloc(b, &b->d_counters, 1)))) {
+        batch_release(b);
+        return rc;
+    }
+    if (rc) {
         batch_release(b);
         return rc;
     }
     cudaError_t ce = cudaMemsetAsync(kj.stats, 0, 4 * sizeof(unsigned long long), s);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(b->d_counters, 0, sizeof(unsigned long long), s);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(b->d_jobs, &kj, sizeof kj, cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(b->d_item_start, starts, sizeof starts, cudaMemcpyHostToDevice, s);
     if (ce != cudaSuccess) {
         batch_release(b);
         return set_error(HWC_ERR_CUDA, "setup: %s", cudaGetErrorString(ce));
     }
-    LaunchShape sh;
-    rc = choose_shape((int)kj.d, kj.method, kj.words, kj.smem_bytes, false, &sh);
-    if (rc == HWC_OK) rc = launch_plain(b->d_jobs, kj, sh, s);
+    rc = launch_persistent((int)kj.d, kj.method, kj.words, b->d_jobs, b->d_item_start, 1, starts[1],
+                           b->d_counters, kj.smem_bytes, sh, s);
     if (rc == HWC_OK) {
         ce = cudaMemcpyAsync(counts, kj.member_counts, count * g * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
         if (ce == cudaSuccess) ce = cudaMemcpyAsync(sqf, kj.member_sqf, count, cudaMemcpyDeviceToHost, s);
