@@ -196,7 +196,7 @@ class ClockSampler:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("count_kernels.cu", "fanout_kernels.cu", "count_common.cuh", "hwc_internal.cuh"):
+    for f in ("count_kernels.cu", "fanout.cuh", "horner.cuh", "count_common.cuh", "hwc_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1805_11991_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -212,7 +212,7 @@ def profiled_traffic():
         return None
     if d.get("kernel_source_hash") != kernel_source_hash():
         return None
-    return d.get("dram_bytes_per_launch")
+    return d.get("dram_bytes_per_step")
 
 
 # ---------------------------------------------------------------------------
