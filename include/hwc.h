@@ -129,8 +129,14 @@ int hwc_family_size(uint32_t q, const hwc_family_t *fam, uint64_t *n);
 #define HWC_FLAG_PLAIN 0x1u       /* one launch per job (no persistent queue)  */
 #define HWC_FLAG_GRAPH 0x2u       /* capture the launch sequence in a CUDA graph */
 #define HWC_FLAG_HORNER 0x4u      /* force the per-member Horner kernel        */
+/* Kernels: enumerated families with q <= 31 use the two-level fan-out (q^2
+ * members sharing c_2..c_d per warp), q <= 63 the one-level c_0 fan-out (q
+ * members per warp), everything else (sampled families, larger q) the
+ * per-member Horner kernel.  All give identical counts. */
 #define HWC_FLAG_NO_TUNE 0x8u     /* skip the autotuner, use defaults          */
 #define HWC_FLAG_TIMING 0x10u     /* time the count kernel(s) with CUDA events */
+#define HWC_FLAG_FAN1 0x20u       /* one-level c_0 fan-out even where the
+                                     two-level (c_1, c_0) kernel applies */
 
 /* Histogram of (#C(F_q), ..., #C(F_{q^g})) over the square-free members
  * [first, first+count) of the family (Algorithm 1 lines 3-17 and 21, every
@@ -143,8 +149,9 @@ int hwc_count(uint32_t g, uint32_t q, const hwc_family_t *fam, uint64_t first,
 /* Per-member counts (for checking): counts[i*g + k-1] = #C(F_{q^k}) and
  * sqf[i] = 1 if member first+i is square-free.  With unfiltered = 0 the
  * counts of non-square-free members are 0; with unfiltered = 1 they are the
- * point-count formula applied anyway.  flags: 0 or HWC_FLAG_HORNER (use the
- * per-member kernel even where the c_0 fan-out kernel applies).  `counts`
+ * point-count formula applied anyway.  flags: 0, HWC_FLAG_HORNER (use the
+ * per-member kernel everywhere) or HWC_FLAG_FAN1 (one-level fan-out where the
+ * two-level kernel would apply).  `counts`
  * (count*g int32) and `sqf` (count bytes) are HOST arrays.  Synchronous. */
 int hwc_count_members(uint32_t g, uint32_t q, const hwc_family_t *fam,
                       uint64_t first, uint64_t count, int unfiltered, uint32_t flags,

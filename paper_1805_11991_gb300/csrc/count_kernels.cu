@@ -81,6 +81,11 @@ KernelFn fan_kernel(int D, int W, bool persistent)
     }
 }
 
+KernelFn fan2_kernel(int D)
+{
+    return D <= 6 ? fan2_kernel_a(D) : fan2_kernel_b(D);
+}
+
 static KernelFn persistent_fn(int D)
 {
     return horner_kernel(D, 1);
@@ -96,7 +101,7 @@ int prepare_count_kernels(void)
     if (dev >= 0 && dev < 64 && done[dev]) return HWC_OK;
     const int optin = (int)device_smem_optin();
     for (int D = 3; D <= kMaxD; ++D) {
-        for (KernelFn fn : {persistent_fn(D), fan_kernel(D, 1, true), fan_kernel(D, 2, true)}) {
+        for (KernelFn fn : {persistent_fn(D), fan_kernel(D, 1, true), fan_kernel(D, 2, true), fan2_kernel(D)}) {
             if (!fn) continue;   // no kernel for this degree and row width
             cudaFuncAttributes fa{};
             HWC_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));   // static smem counts against the limit
@@ -126,6 +131,7 @@ uint32_t device_smem_optin(void)
 
 static KernelFn kernel_for(int D, uint32_t method, uint32_t words, bool persistent)
 {
+    if (method == 2) return fan2_kernel(D);
     if (method == 1) return fan_kernel(D, (int)words, persistent);
     (void)persistent;   // every run is a persistent launch (a plain run has one job per launch)
     return persistent_fn(D);

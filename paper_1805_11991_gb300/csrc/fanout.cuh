@@ -45,14 +45,14 @@ struct Planes {
     uint32_t p[8];
 };
 
-// Horner in the log domain for h(x) = sum_{i>=1} c_i x^(i-1) with explicit
+// Horner in the log domain for h(x) = sum_{i>=LOW} c_i x^(i-LOW) with explicit
 // zero handling; returns log h(x) or L when h(x) = 0.
 template <int D>
 struct LamV {
     uint32_t v[D + 1];
 };
 
-template <int D, class Tab>
+template <int D, int LOW, class Tab>
 __device__ __noinline__ uint32_t slow_log_h(const Tab T, uint32_t L, uint32_t cap, const LamV<D> lamv,
                                             uint32_t nz, uint32_t j)
 {
@@ -60,7 +60,7 @@ __device__ __noinline__ uint32_t slow_log_h(const Tab T, uint32_t L, uint32_t ca
     uint32_t l = lam[D];
     bool zero = false;
 #pragma unroll
-    for (int i = D - 1; i >= 1; --i) {
+    for (int i = D - 1; i >= LOW; --i) {
         if (!zero) l = addmod(l, j, L);
         if ((nz >> i) & 1u) {
             if (zero) {
@@ -90,10 +90,11 @@ struct HChain {
     bool none;           // h = c_D x^(D-1)
 };
 
-template <int D>
+// LOW = 1: h over c_1..c_d (one-level fan-out); LOW = 2: v over c_2..c_d
+template <int D, int LOW = 1>
 __device__ __forceinline__ void make_hchain(HChain<D> &H, const uint32_t (&lam)[D + 1], uint32_t nz, uint32_t L)
 {
-    const uint32_t nzh = nz & ~1u;       // positions 1..D-1
+    const uint32_t nzh = nz & ~((1u << LOW) - 1u);   // positions LOW..D-1
     H.none = nzh == 0;
     const int i1 = H.none ? 0 : 31 - __clz(nzh);
     const int is = H.none ? D : __ffs(nzh) - 1;
@@ -107,26 +108,26 @@ __device__ __forceinline__ void make_hchain(HChain<D> &H, const uint32_t (&lam)[
     for (int i = D - 1; i >= 0; --i) {
         H.dli[i] = 0;
         H.gpi[i] = 0;
-        if (i >= 1 && i < i1 && ((nzh >> i) & 1u)) {
+        if (i >= LOW && i < i1 && ((nzh >> i) & 1u)) {
             H.dli[i] = addmod(lp, L - lam[i], L);
             H.gpi[i] = (uint32_t)(ip - i);
             lp = lam[i];
             ip = i;
         }
     }
-    const uint32_t full2 = ((1u << (D - 1)) - 1u) & ~1u;   // bits 1..D-2
+    const uint32_t full2 = ((1u << (D - 1)) - 1u) & ~((1u << LOW) - 1u);   // bits LOW..D-2
     H.dense = (nzh == full2) ? 2 : 0;
 }
 
 // chain steps for coefficient patterns with zeros below the lead (any gaps);
 // out of line: such groups are a few percent of a family
-template <int D, bool TRIPLE, class Tab>
+template <int D, bool TRIPLE, int LOW, class Tab>
 __device__ __noinline__ void general_chain(const Tab T, uint32_t L, uint32_t bar, uint32_t cap,
                                            const HChain<D> H, uint32_t xA, uint32_t xB, uint32_t &uA,
                                            uint32_t &uB)
 {
 #pragma unroll
-    for (int i = D - 2; i >= 1; --i) {
+    for (int i = D - 2; i >= LOW; --i) {
         if (H.gpi[i] == 0) continue;
         uint32_t sA, sB;
         if (H.gpi[i] == 1) {
@@ -142,8 +143,9 @@ __device__ __noinline__ void general_chain(const Tab T, uint32_t L, uint32_t bar
     }
 }
 
-// log y for x = alpha^j (y = x h(x)), or L when y = 0; two x per lane.
-template <int D, bool TRIPLE, class Tab>
+// log y for x = alpha^j (y = x^LOW h(x) = sum_{i>=LOW} c_i x^i), or L when
+// y = 0; two x per lane.
+template <int D, bool TRIPLE, class Tab, int LOW = 1>
 __device__ __forceinline__ void log_y_pair(const Tab T, uint32_t L, uint32_t bar, const HChain<D> &H,
                                            const uint32_t (&lam)[D + 1], uint32_t nz, uint32_t xA,
                                            uint32_t xB, uint32_t &yA, uint32_t &yB)
@@ -169,13 +171,13 @@ __device__ __forceinline__ void log_y_pair(const Tab T, uint32_t L, uint32_t bar
     }
     if (H.dense == 2) {
 #pragma unroll
-        for (int i = D - 3; i >= 1; --i) {
+        for (int i = D - 3; i >= LOW; --i) {
             const uint32_t zA = T[uA], zB = T[uB];
             uA = chain_step<TRIPLE>(zA, H.dli[i], xA, L, cap);
             uB = chain_step<TRIPLE>(zB, H.dli[i], xB, L, cap);
         }
     } else {
-        general_chain<D, TRIPLE>(T, L, bar, cap, H, xA, xB, uA, uB);
+        general_chain<D, TRIPLE, LOW>(T, L, bar, cap, H, xA, xB, uA, uB);
     }
     const uint32_t zA = T[uA], zB = T[uB];
     // y = alpha^(lam_last + z + tail*j)
@@ -195,12 +197,12 @@ __device__ __forceinline__ void log_y_pair(const Tab T, uint32_t L, uint32_t bar
 #pragma unroll
         for (int i = 0; i <= D; ++i) lv.v[i] = lam[i];
         if (pA) {
-            const uint32_t lh = slow_log_h<D>(T, L, cap, lv, nz, xA);
-            yA = lh == L ? L : addmod(lh, xA, L);
+            const uint32_t lh = slow_log_h<D, LOW>(T, L, cap, lv, nz, xA);
+            yA = lh == L ? L : addmod(lh, LOW == 1 ? xA : mulmod_small(LOW, xA, L, bar), L);
         }
         if (pB) {
-            const uint32_t lh = slow_log_h<D>(T, L, cap, lv, nz, xB);
-            yB = lh == L ? L : addmod(lh, xB, L);
+            const uint32_t lh = slow_log_h<D, LOW>(T, L, cap, lv, nz, xB);
+            yB = lh == L ? L : addmod(lh, LOW == 1 ? xB : mulmod_small(LOW, xB, L, bar), L);
         }
     }
 }

@@ -1,0 +1,309 @@
+// fanout2.cuh -- two-level (c_1, c_0) fan-out count kernel for enumerated
+// families with q <= 31; instantiated per degree in fan2_a.cu and fan2_b.cu.
+//
+// q^2 consecutive members of a family differ only in c_1 = b and c_0 = c:
+// f_{b,c}(x) = u(x) + b x + c with u(x) = sum_{i>=2} c_i x^i.  One warp takes
+// such a group.  For 64 points x = alpha^j at a time the warp evaluates u(x)
+// by the Zech-index Horner chain over c_2..c_d (one chain per x, shared by all
+// q^2 members) and stages log u(x) in shared memory.  Each lane owns one value
+// of b (several lanes per b when q < 16, splitting the points) and, per point,
+// does one Zech addition, y_b = u + b x = b x (1 + u / (b x)) (eq. 2.1), and
+// reads the fan-out row of y_b: its q bits say chi(y_b + c) = -1 for every
+// c at once.  A lane sums its rows per bit position with bit-sliced
+// carry-save counters and from time to time adds the per-position counts
+// into the group's (b, c) accumulators in shared memory.  With n_0(b) the
+// number of x with y_b(x) = 0 (x = 0 included) and z(b, c) the rare x with
+// y_b(x) = -c != 0:
+//     sum_x chi(f_{b,c}(x)) = n_0 chi(c) + (Q - n_0) - 2 cnt(b, c) - z(b, c),
+//     #C_k(f_{b,c}) = Q + sum_x chi(f_{b,c}(x)) + 1 + chi(f(inf))   (Sec. 1.1).
+// Per point and member this is 1/q Zech additions and one row bit; the chain
+// for u and every per-group cost are shared by q^2 members.
+#pragma once
+#include "fanout.cuh"
+
+namespace hwc {
+namespace {
+
+constexpr int kFan2Warps = 4;                 // warps per CTA
+constexpr int kFan2Planes = 10;               // per-lane counts < 1024 between flushes
+constexpr uint32_t kFan2FlushBlocks = 127;    // 8-input blocks per lane between flushes
+
+// add 8 row words into 10 bit-sliced planes (carry-save tree, ripple of the eights)
+__device__ __forceinline__ void add8_p10(uint32_t (&P)[kFan2Planes], const uint32_t (&a)[8])
+{
+    uint32_t tA, tB, fA, fB, e;
+    csa(tA, P[0], P[0], a[0], a[1]);
+    csa(tB, P[0], P[0], a[2], a[3]);
+    csa(fA, P[1], P[1], tA, tB);
+    csa(tA, P[0], P[0], a[4], a[5]);
+    csa(tB, P[0], P[0], a[6], a[7]);
+    csa(fB, P[1], P[1], tA, tB);
+    csa(e, P[2], P[2], fA, fB);
+#pragma unroll
+    for (int b = 3; b < kFan2Planes; ++b) {
+        const uint32_t c = P[b] & e;
+        P[b] ^= e;
+        e = c;
+    }
+}
+
+// add the per-position counts of the planes into acc[c] (2 per row bit), clear
+__device__ __forceinline__ void flush_planes(uint32_t (&P)[kFan2Planes], uint32_t *acc_b, uint32_t q,
+                                             bool role)
+{
+    if (role) {
+        for (uint32_t c = 0; c < q; ++c) {
+            uint32_t v = 0;
+#pragma unroll
+            for (int b = 0; b < kFan2Planes; ++b) v |= ((P[b] >> c) & 1u) << b;
+            if (v) atomicAdd(&acc_b[c], 2 * v);
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < kFan2Planes; ++b) P[b] = 0;
+}
+
+// points of one field for the whole group (all q^2 members), lane role (b, s)
+template <int D, bool TRIPLE>
+__device__ __forceinline__ void group2_field(const TabS T, const KJob &J, int k, const uint8_t *smem,
+                                             const HChain<D> &H, const uint32_t (&lam)[D + 1], uint32_t nz,
+                                             uint32_t *Us, uint32_t *acc, uint32_t *n0s, int lane, bool role,
+                                             uint32_t b, uint32_t s, uint32_t S)
+{
+    const uint32_t L = J.L[k], q = J.q;
+    const uint32_t cap = TRIPLE ? 3 * L : 2 * L;
+    const uint32_t bar = J.barrett[k];
+    const uint32_t *rows = reinterpret_cast<const uint32_t *>(smem + J.row_off[k]);
+    const uint8_t *zdig = smem + J.zdig_off[k];
+    const uint32_t zdiv = J.zdiv[k];
+    const uint32_t *coefk = reinterpret_cast<const uint32_t *>(smem) + J.coef_off[k];
+    const uint32_t lam_b = (role && b != 0) ? coefk[b] : L;
+    uint32_t *acc_b = acc + b * q;
+    uint32_t P[kFan2Planes];
+#pragma unroll
+    for (int p = 0; p < kFan2Planes; ++p) P[p] = 0;
+    uint32_t nblk = 0, n0 = 0;
+    for (uint32_t j0 = 0; j0 < L; j0 += 64) {
+        // log u(x) for the batch, two points per lane, staged for all lanes
+        const uint32_t xA = j0 + lane, xB = j0 + 32 + lane;
+        uint32_t uA, uB;
+        log_y_pair<D, TRIPLE, TabS, 2>(T, L, bar, H, lam, nz, xA < L ? xA : 0, xB < L ? xB : 0, uA, uB);
+        Us[lane] = uA;
+        Us[32 + lane] = uB;
+        __syncwarp();
+        const uint32_t nb = min(64u, L - j0);              // points in this batch
+        const uint32_t T_in = (nb + S - 1) / S;            // inputs per lane (uniform)
+        for (uint32_t t0 = 0; t0 < T_in; t0 += 8) {
+            uint32_t a[8];
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+                const uint32_t i = s + (t0 + v) * S;
+                const bool ok = role && i < nb;
+                const uint32_t U = Us[ok ? i : 0];
+                const uint32_t xi = j0 + i;
+                // y_b = u + b x: Zech addition in the log domain
+                const uint32_t lbx = addmod(lam_b == L ? 0u : lam_b, ok ? xi : 0u, L);
+                const uint32_t n = U + (L - lbx);            // in [1, 2L]
+                const uint32_t z = T[n];
+                uint32_t ly;
+                if (b == 0) ly = U;                          // y_0 = u
+                else if (U >= L) ly = lbx;                   // u = 0: y = b x
+                else ly = (z >= cap) ? L : addmod(lbx, z, L);
+                const bool zero = ly >= L;
+                const uint32_t r = rows[zero ? 0 : ly];
+                a[v] = (ok && !zero) ? (r & 0x7FFFFFFFu) : 0u;
+                n0 += (ok && zero) ? 1u : 0u;
+                if (ok && !zero && (r >> 31))   // y in F_q^x: y + c = 0 for one digit c
+                    atomicAdd(&acc_b[zdig[zdiv ? __umulhi(ly, zdiv) : ly]], 1u);
+            }
+            add8_p10(P, a);
+            if (++nblk == kFan2FlushBlocks) {
+                flush_planes(P, acc_b, q, role);
+                nblk = 0;
+            }
+        }
+        __syncwarp();   // Us is rewritten by the next batch
+    }
+    flush_planes(P, acc_b, q, role);
+    if (role && n0) atomicAdd(&n0s[b], n0);
+}
+
+// one group of q^2 members (c_1, c_0 free) for one warp
+template <int D>
+__device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, const uint8_t *smem,
+                                               uint8_t *wsm, int lane, WarpStats &st)
+{
+    constexpr int G = (D - 1) / 2;
+    const uint32_t q = J.q, qq = q * q;
+    const uint64_t base = (J.first_group + gtile) * qq;
+    uint32_t c[D + 1];
+    decode_index<D>(J, base, c);
+    c[0] = 0;
+    c[1] = 0;
+    uint32_t nz = 0;
+#pragma unroll
+    for (int i = 2; i < D; ++i) nz |= (c[i] != 0 ? 1u : 0u) << i;
+
+    // per-warp scratch: Us[64] | acc[q^2] | n0s[q] | sqf[ceil(q^2/32)] | keys[q^2] (u64)
+    uint32_t *Us = reinterpret_cast<uint32_t *>(wsm);
+    uint32_t *acc = Us + 64;
+    uint32_t *n0s = acc + qq;
+    uint32_t *sqfw = n0s + q;
+    const uint32_t nw = (qq + 31) / 32;
+    unsigned long long *keys =
+        reinterpret_cast<unsigned long long *>(wsm + ((4u * (64 + qq + q + nw) + 7u) & ~7u));
+
+    const uint16_t *s16 = reinterpret_cast<const uint16_t *>(smem);
+    const uint32_t *s32 = reinterpret_cast<const uint32_t *>(smem);
+    const uint8_t *mulT = smem + J.fq_off;
+    const uint8_t *subT = mulT + qq;
+    const uint8_t *invT = subT + qq;
+
+    // square-freeness of the q^2 members, 32 at a time
+    uint32_t anyv = 0, anys = 0;
+    for (uint32_t t = 0; t < nw; ++t) {
+        const uint32_t m = t * 32 + lane;
+        const uint64_t idx = base + m;
+        const bool v = m < qq && idx >= J.first && idx < J.first + J.count;
+        bool sq = false;
+        if (v) {
+            uint32_t cm[D + 1];
+#pragma unroll
+            for (int i = 0; i <= D; ++i) cm[i] = c[i];
+            cm[0] = m % q;
+            cm[1] = m / q;
+            sq = squarefree_digits<D>(mulT, subT, invT, q, J.p, cm);
+        }
+        const unsigned vm = __ballot_sync(0xFFFFFFFFu, v);
+        const unsigned sm = __ballot_sync(0xFFFFFFFFu, sq);
+        if (lane == 0) {
+            sqfw[t] = sm;
+            st.examined += __popc(vm);
+            st.sqf += __popc(sm);
+        }
+        anyv |= vm;
+        anys |= sm;
+        if (m < qq) keys[m] = 0;
+    }
+    __syncwarp();
+    if ((J.unfiltered ? anyv : anys) == 0) {
+        if (J.member_counts) {
+            for (uint32_t m = lane; m < qq; m += 32) {
+                const uint64_t idx = base + m;
+                if (idx < J.first || idx >= J.first + J.count) continue;
+#pragma unroll
+                for (int k = 0; k < G; ++k) J.member_counts[(idx - J.first) * G + k] = 0;
+                J.member_sqf[idx - J.first] = 0;
+            }
+        }
+        return;
+    }
+
+    // lane roles: S lanes per value b of c_1, each taking every S-th point
+    const uint32_t S = 32 / q;
+    const bool role = (uint32_t)lane < S * q;
+    const uint32_t b = role ? (uint32_t)lane % q : 0;
+    const uint32_t s = role ? (uint32_t)lane / q : 0;
+
+#pragma unroll 1
+    for (int k = 0; k < G; ++k) {
+        const uint32_t L = J.L[k], Q = J.Q[k];
+        const uint32_t *coefk = s32 + J.coef_off[k];
+        uint32_t lam[D + 1];
+#pragma unroll
+        for (int i = 0; i <= D; ++i) lam[i] = coefk[c[i]];
+        HChain<D> H;
+        make_hchain<D, 2>(H, lam, nz, L);
+        for (uint32_t m = lane; m < qq; m += 32) acc[m] = 0;
+        if ((uint32_t)lane < q) n0s[lane] = 0;
+        __syncwarp();
+        if (J.tab_kind[k] == kTabTripleSmem)
+            group2_field<D, true>(TabS{s16 + J.tab_off[k]}, J, k, smem, H, lam, nz, Us, acc, n0s, lane, role, b,
+                                  s, S);
+        else
+            group2_field<D, false>(TabS{s16 + J.tab_off[k]}, J, k, smem, H, lam, nz, Us, acc, n0s, lane, role, b,
+                                   s, S);
+        __syncwarp();
+        int inf = 1;
+        if (D == 2 * G + 2) inf += (lam[D] & 1u) ? -1 : 1;
+        for (uint32_t m = lane; m < qq; m += 32) {
+            const uint32_t bb = m / q, cc = m % q;
+            const uint32_t n0 = n0s[bb] + 1;                 // + x = 0 (y = 0)
+            const uint32_t lc = coefk[cc];
+            const int chi_c = (cc == 0) ? 0 : ((lc & 1u) ? -1 : 1);
+            const int S_ = (int)n0 * chi_c + (int)(Q - n0) - (int)acc[m];
+            const int N = (int)Q + S_ + inf;
+            if (J.member_counts) {
+                const uint64_t idx = base + m;
+                if (idx >= J.first && idx < J.first + J.count) {
+                    const bool sq = (sqfw[m / 32] >> (m % 32)) & 1u;
+                    J.member_counts[(idx - J.first) * G + k] = (sq || J.unfiltered) ? N : 0;
+                    if (k == 0) J.member_sqf[idx - J.first] = sq ? 1 : 0;
+                }
+            }
+            const int a = (int)Q + 1 - N;   // eq. 1.1
+            keys[m] |= (unsigned long long)((uint32_t)(a + 32768) & 0xFFFFu) << (16 * k);
+        }
+        __syncwarp();
+    }
+    if (J.member_counts) return;
+    for (uint32_t t = 0; t < nw; ++t) {
+        const uint32_t m = t * 32 + lane;
+        const bool sq = m < qq && ((sqfw[t] >> lane) & 1u);
+        const unsigned smask = __ballot_sync(0xFFFFFFFFu, sq);
+        if (sq) {
+            const unsigned long long key = keys[m];
+            const unsigned peers = __match_any_sync(smask, key);
+            if (lane == __ffs(peers) - 1) hist_insert(J, key, __popc(peers));
+        }
+    }
+    __syncwarp();
+}
+
+template <int D>
+__global__ void __launch_bounds__(kFan2Warps * 32, 4)
+    k_fan2_persistent(const KJob *__restrict__ jobs, const uint64_t *__restrict__ item_start, uint32_t n_jobs,
+                      uint64_t n_items, unsigned long long *counter, uint32_t item_tiles)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ unsigned long long s_item;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwp = blockDim.x >> 5;
+    int cur = -1;
+    WarpStats st;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1ull);
+        __syncthreads();
+        const uint64_t item = s_item;
+        __syncthreads();
+        if (item >= n_items) break;
+        uint32_t lo = 0, hi = n_jobs;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (item_start[mid] <= item) lo = mid;
+            else hi = mid;
+        }
+        const int jb = (int)lo;
+        if (jb != cur) {
+            if (cur >= 0) flush_stats(jobs[cur], st, lane);
+            stage_job(jobs[jb], smem);
+            __syncthreads();
+            cur = jb;
+        }
+        const KJob &J = jobs[jb];
+        uint8_t *wsm = smem + J.warp_off + warp * J.warp_bytes;
+        const uint64_t t0 = (item - item_start[jb]) * item_tiles;
+        const uint64_t t1 = min(t0 + item_tiles, J.n_tiles);
+        for (uint64_t t = t0 + warp; t < t1; t += nwp) process_group2<D>(J, t, smem, wsm, lane, st);
+        __syncthreads();
+    }
+    if (cur >= 0) flush_stats(jobs[cur], st, lane);
+}
+
+template <int D>
+const void *fan2_pick()
+{
+    return (const void *)k_fan2_persistent<D>;
+}
+
+}  // namespace
+}  // namespace hwc

@@ -104,7 +104,8 @@ struct KJob {
     uint32_t smem_u16;                // u16 words of zech2 tables staged in smem
     uint32_t smem_bytes;              // total dynamic smem for this job
     // c_0 fan-out (method 1): groups of q members that differ only in c_0
-    uint32_t method;                  // 0 Horner tiles of 32 members, 1 fan-out groups
+    uint32_t method;                  // 0 Horner tiles of 32 members, 1 fan-out groups of q,
+                                      // 2 two-level fan-out groups of q^2
     uint32_t words;                   // row words: 1 (q <= 31) or 2 (q <= 63)
     uint64_t first_group;             // group of member `first`
     const void *rows[kMaxG];          // d_rows32 / d_rows64
@@ -112,6 +113,7 @@ struct KJob {
     uint32_t row_off[kMaxG];          // byte offset of the rows in smem
     uint32_t zdig_off[kMaxG];         // byte offset of zdig in smem
     uint32_t zdiv[kMaxG];             // ceil(2^32 / (L/(q-1))): l / s by a high multiply
+    uint32_t warp_off, warp_bytes;    // per-warp scratch in smem (method 2)
     const uint8_t *fq_mul, *fq_sub, *fq_inv;   // digit arithmetic of F_q (fan-out jobs)
     uint32_t fq_off;                  // byte offset of mul | sub | inv in smem
     // outputs
@@ -165,6 +167,19 @@ const void *fan_kernel_b(int D, int W, bool persistent);   // fanout_b.cu, D = 5
 const void *fan_kernel_c(int D, int W, bool persistent);   // fanout_c.cu, D = 6
 const void *fan_kernel_d(int D, int W, bool persistent);   // fanout_d.cu, D = 7
 const void *fan_kernel_f(int D, int W, bool persistent);   // fanout_f.cu, D = 8
+// two-level fan-out kernels (fanout2.cuh), q <= 31
+const void *fan2_kernel(int D);
+const void *fan2_kernel_a(int D);   // fan2_a.cu, D = 3..6
+const void *fan2_kernel_b(int D);   // fan2_b.cu, D = 7..10
+constexpr int kFan2WarpsHost = 4;   // warps per CTA of the two-level kernel
+// per-warp scratch bytes of the two-level kernel for q
+inline uint32_t fan2_warp_bytes(uint32_t q)
+{
+    const uint32_t qq = q * q, nw = (qq + 31) / 32;
+    uint32_t b = (4u * (64 + qq + q + nw) + 7u) & ~7u;
+    b += 8u * qq;
+    return (b + 15u) & ~15u;
+}
 const void *fan_kernel_e(int D, int W, bool persistent);   // fanout_e.cu, D = 9, 10
 // hash slots for a job of `count` members (power of two)
 uint32_t hash_capacity(uint32_t g, uint32_t q, uint64_t count, uint32_t scale);

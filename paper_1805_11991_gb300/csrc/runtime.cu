@@ -107,10 +107,12 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit)
         return 0;
     };
     auto fan_bytes = [&](void) -> uint64_t {
-        if (j.method != 1) return 0;
+        if (j.method == 0) return 0;
         uint64_t b = 0;
         for (uint32_t k = 0; k < j.g; ++k) b += 4ull * j.words * j.L[k] + ((j.q + 15) / 16) * 16;
-        return b + ((2ull * j.q * j.q + j.q + 15) / 16) * 16;
+        b += ((2ull * j.q * j.q + j.q + 15) / 16) * 16;
+        if (j.method == 2) b += 16 + (uint64_t)kFan2WarpsHost * fan2_warp_bytes(j.q);
+        return b;
     };
     auto bytes_for = [&](void) {
         uint64_t u16 = 0;
@@ -125,6 +127,9 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit)
         kind[big] = (kind[big] == kTabTripleSmem && j.zech2[big]) ? kTabDoubleSmem : kTabDoubleGlobal;
     }
     if (bytes_for() > smem_limit) return false;
+    if (j.method == 2)   // the two-level kernel reads every Zech table from shared memory
+        for (uint32_t k = 0; k < j.g; ++k)
+            if (kind[k] == kTabDoubleGlobal) return false;
     uint32_t off = 0;
     for (uint32_t k = 0; k < kMaxG; ++k) {
         j.tab_kind[k] = k < j.g ? kind[k] : kTabDoubleGlobal;
@@ -141,7 +146,7 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit)
     for (uint32_t k = 0; k < kMaxG; ++k) {
         j.row_off[k] = bytes;
         j.zdig_off[k] = bytes;
-        if (j.method == 1 && k < j.g) {
+        if (j.method != 0 && k < j.g) {
             bytes += 4 * j.words * j.L[k];
             bytes = (bytes + 15) / 16 * 16;
             j.zdig_off[k] = bytes;
@@ -149,7 +154,15 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit)
         }
     }
     j.fq_off = bytes;
-    if (j.method == 1) bytes += ((2 * j.q * j.q + j.q + 15) / 16) * 16;
+    if (j.method != 0) bytes += ((2 * j.q * j.q + j.q + 15) / 16) * 16;
+    j.warp_off = 0;
+    j.warp_bytes = 0;
+    if (j.method == 2) {
+        bytes = (bytes + 15) / 16 * 16;
+        j.warp_off = bytes;
+        j.warp_bytes = fan2_warp_bytes(j.q);
+        bytes += kFan2WarpsHost * j.warp_bytes;
+    }
     j.smem_bytes = bytes;
     return true;
 }
@@ -200,6 +213,8 @@ int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n, uint32_t flags)
     kj.n_tiles = (jb.count + kTileMembers - 1) / kTileMembers;
     // enumerated families with q <= 63: groups of q members share all but c_0
     const bool fan = !(flags & HWC_FLAG_HORNER) && jb.family.kind != HWC_FAM_MONIC_NOSUB_SAMPLED && jb.q <= 63;
+    // (method chosen below: two-level fan-out for q <= 31, one-level up to 63,
+    // per-member Horner otherwise or when a layout does not fit)
     for (uint32_t k = 1; k <= jb.g; ++k) {
         const Tables *t = nullptr;
         rc = tables_cached(jb.q, k, &t);
@@ -224,6 +239,14 @@ int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n, uint32_t flags)
         kj.zdiv[k - 1] = sdiv == 1 ? 0u : (uint32_t)(((1ull << 32) + sdiv - 1) / sdiv);
     }
     const uint32_t limit = device_smem_optin() - 4096;   // static smem of the kernels
+    if (fan && jb.q <= 31 && !(flags & HWC_FLAG_FAN1)) {
+        // two-level fan-out: groups of q^2 members
+        kj.method = 2;
+        kj.words = 1;
+        kj.first_group = jb.first / ((uint64_t)jb.q * jb.q);
+        kj.n_tiles = jb.count ? (jb.first + jb.count - 1) / ((uint64_t)jb.q * jb.q) - kj.first_group + 1 : 0;
+        if (layout_job_smem(kj, limit)) return HWC_OK;
+    }
     if (fan) {
         kj.method = 1;
         kj.words = jb.q <= 31 ? 1 : 2;
@@ -391,8 +414,8 @@ int hwc::choose_shape(int D, uint32_t method, uint32_t words, uint32_t smem, boo
 {
     const int sms = device_sm_count();
     int best_block = 256, best_warps = -1, best_ctas = 1;
-    const int blocks[2] = {256, 128};
-    for (int bi = 0; bi < (method == 1 ? 1 : 2); ++bi) {
+    const int blocks[2] = {method == 2 ? kFan2WarpsHost * 32 : 256, 128};
+    for (int bi = 0; bi < (method == 0 ? 2 : 1); ++bi) {
         const int block = blocks[bi];
         int ctas = 0;
         int rc = max_ctas_per_sm(D, method, words, block, smem, persistent, &ctas);
@@ -407,7 +430,7 @@ int hwc::choose_shape(int D, uint32_t method, uint32_t words, uint32_t smem, boo
     if (best_warps <= 0) return set_error(HWC_ERR_TOO_LARGE, "no CTA fits %u bytes of shared memory", smem);
     out->block = best_block;
     out->grid = sms * best_ctas;
-    out->item_tiles = (best_block / 32) * (method == 1 ? 1 : 2);
+    out->item_tiles = (best_block / 32) * (method == 0 ? 2 : 1);
     return HWC_OK;
 }
 
@@ -426,14 +449,19 @@ static int batch_create_impl(const hwc_job_t *jobs, size_t n, uint32_t flags, ui
     hwc_batch *b = new hwc_batch();
     b->flags = flags;
     cudaGetDevice(&b->device);
-    // order jobs by degree (stable), remember where each caller's job went
+    // descriptors in the caller's order, then ordered by kernel (degree, method,
+    // row width) so that jobs of one kernel share a persistent launch
+    std::vector<HostJob> filled(n);
+    for (size_t i = 0; i < n; ++i) {
+        filled[i].job = jobs[i];
+        rc = fill_kjob(jobs[i], filled[i].kj, &filled[i].fam_n, flags);
+        if (rc) { batch_release(b); return rc; }
+    }
     std::vector<size_t> order(n);
     std::iota(order.begin(), order.end(), 0);
-    // group key: degree, then kernel (fan-out for enumerated q <= 63 unless forced)
     auto gkey = [&](size_t x) {
-        const hwc_job_t &j = jobs[x];
-        const bool fan = !(flags & HWC_FLAG_HORNER) && j.family.kind != HWC_FAM_MONIC_NOSUB_SAMPLED && j.q <= 63;
-        return std::make_tuple(j.family.degree, fan ? 1u : 0u, fan ? (j.q <= 31 ? 1u : 2u) : 0u);
+        const KJob &k = filled[x].kj;
+        return std::make_tuple(k.d, k.method, k.words);
     };
     std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return gkey(x) < gkey(y); });
     b->pos.resize(n);
@@ -442,9 +470,7 @@ static int batch_create_impl(const hwc_job_t *jobs, size_t n, uint32_t flags, ui
         const size_t i = order[r];
         b->pos[i] = r;
         HostJob &hj = b->jobs[r];
-        hj.job = jobs[i];
-        rc = fill_kjob(jobs[i], hj.kj, &hj.fam_n, flags);
-        if (rc) { batch_release(b); return rc; }
+        hj = filled[i];
         KJob &kj = hj.kj;
         const uint32_t cap = hash_capacity(kj.g, kj.q, jobs[i].count, cap_scale);
         kj.hmask = cap - 1;
@@ -684,7 +710,7 @@ extern "C" int hwc_count_members(uint32_t g, uint32_t q, const hwc_family_t *fam
     rc = prepare_count_kernels();
     if (rc) return rc;
     KJob kj;
-    rc = fill_kjob(j, kj, &fam_n, flags & HWC_FLAG_HORNER);
+    rc = fill_kjob(j, kj, &fam_n, flags & (HWC_FLAG_HORNER | HWC_FLAG_FAN1));
     if (rc) return rc;
     if (count == 0) return HWC_OK;
     kj.unfiltered = unfiltered ? 1u : 0u;

@@ -228,7 +228,7 @@ void server_loop(hwc_server *s)
                 const uint64_t left = q->kj.n_tiles - q->next_tile;
                 const uint64_t t = std::min(left, share);
                 took[r] = t;
-                if (q->kj.method == 1) {
+                if (q->kj.method != 0) {
                     // fan-out tiles are groups; the member range stays the request's
                     sl.first_group = q->kj.first_group + q->next_tile;
                 } else {

@@ -42,9 +42,10 @@ def test_batch_equals_alone(flags):
     n = b.kernel_launches()
     def key(s):
         fan = s.kind != MONIC_NOSUB_SAMPLED and s.q <= 63
-        return (s.degree, fan, (1 if s.q <= 31 else 2) if fan else 0)
+        method = (2 if s.q <= 31 else 1) if fan else 0
+        return (s.degree, method, (1 if s.q <= 31 else 2) if fan else 0)
     groups = len({key(s) for s in MIX})
-    assert n == (2 + len(MIX) if flags & hwc.FLAG_PLAIN else 2 + groups)
+    assert n == 2 + (len(MIX) if flags & hwc.FLAG_PLAIN else groups)
     b.close()
 
 

@@ -51,16 +51,19 @@ MEMBER_CASES = [
 
 @pytest.mark.parametrize("spec", MEMBER_CASES, ids=lambda s: f"g{s.g}q{s.q}k{s.kind}d{s.degree}@{s.first}+{s.n()}")
 @pytest.mark.parametrize("unfiltered", [False, True])
-@pytest.mark.parametrize("kernel", ["auto", "horner"])
+@pytest.mark.parametrize("kernel", ["auto", "fan1", "horner"])
 def test_members_match_oracle(orc, spec, unfiltered, kernel):
-    """'auto' takes the c_0 fan-out kernel for enumerated families with
-    q <= 63 and the per-member Horner kernel otherwise; 'horner' forces the
-    latter everywhere."""
+    """'auto' takes the two-level fan-out kernel for enumerated families with
+    q <= 31, the one-level c_0 fan-out up to q = 63 and the per-member Horner
+    kernel otherwise; 'fan1' and 'horner' force the other two."""
     if unfiltered and spec.q > 100:
         pytest.skip("one mode is enough for the slow oracle field")
-    if kernel == "horner" and (spec.kind == MONIC_NOSUB_SAMPLED or spec.q > 63):
+    enumerated = spec.kind != MONIC_NOSUB_SAMPLED
+    if kernel == "horner" and (not enumerated or spec.q > 63):
         pytest.skip("same kernel as 'auto'")
-    flags = hwc.FLAG_HORNER if kernel == "horner" else 0
+    if kernel == "fan1" and (not enumerated or spec.q > 31):
+        pytest.skip("same kernel as 'auto'")
+    flags = {"auto": 0, "fan1": hwc.FLAG_FAN1, "horner": hwc.FLAG_HORNER}[kernel]
     gc, gs = gpu_members(spec, unfiltered=unfiltered, flags=flags)
     oc, os_ = oracle_members(orc, spec, filter=not unfiltered)
     np.testing.assert_array_equal(gs, os_)
@@ -72,7 +75,7 @@ def test_members_match_oracle(orc, spec, unfiltered, kernel):
     JobSpec(3, 7, MONIC_NOSUB, 7), JobSpec(2, 9, ALL_DEG, 5), JobSpec(4, 3, MONIC_NOSUB, 9),
     JobSpec(2, 31, MONIC_NOSUB, 6, 20_000_000, 300_001),
 ], ids=lambda s: f"g{s.g}q{s.q}d{s.degree}@{s.first}")
-@pytest.mark.parametrize("flags", [0, hwc.FLAG_HORNER], ids=["auto", "horner"])
+@pytest.mark.parametrize("flags", [0, hwc.FLAG_FAN1, hwc.FLAG_HORNER], ids=["auto", "fan1", "horner"])
 def test_full_histograms_match_oracle(orc, spec, flags):
     h = gpu_hist(spec, flags)
     assert_hist_equal(h, oracle_hist(orc, spec))
@@ -84,7 +87,7 @@ def test_empty_range():
     assert h.n_total == 0 and h.n_squarefree == 0 and len(h.mult) == 0
 
 
-@pytest.mark.parametrize("flags", [0, hwc.FLAG_HORNER], ids=["auto", "horner"])
+@pytest.mark.parametrize("flags", [0, hwc.FLAG_FAN1, hwc.FLAG_HORNER], ids=["auto", "fan1", "horner"])
 def test_edge_ranges(orc, flags):
     """Last member, single members, and ranges that start and end inside a
     group of q members sharing c_1..c_d (partial fan-out groups)."""
@@ -92,7 +95,9 @@ def test_edge_ranges(orc, flags):
                  JobSpec(2, 31, MONIC_NOSUB, 5, 31 * 100 + 7, 31 * 3 + 11),
                  JobSpec(2, 61, MONIC_NOSUB, 5, 61 * 7 + 40, 61 * 2 + 5),
                  JobSpec(2, 37, MONIC_NOSUB, 6, 37 ** 4 + 30, 20),
-                 JobSpec(3, 13, MONIC_NOSUB, 7, 13 ** 5 + 12, 2)):
+                 JobSpec(3, 13, MONIC_NOSUB, 7, 13 ** 5 + 12, 2),
+                 JobSpec(2, 31, MONIC_NOSUB, 5, 31 * 31 * 5 + 17, 31 * 31 * 2 + 40),
+                 JobSpec(2, 3, ALL_DEG, 6, 5, 1000), JobSpec(2, 5, MONIC_NOSUB, 6, 24, 3000)):
         gc, gs = gpu_members(spec, unfiltered=True, flags=flags)
         oc, os_ = oracle_members(orc, spec, filter=False)
         np.testing.assert_array_equal(gc, oc)
@@ -100,7 +105,7 @@ def test_edge_ranges(orc, flags):
 
 
 @pytest.mark.parametrize("g,q,d", [(2, 5, 5), (2, 3, 6), (3, 3, 7), (2, 7, 6)])
-@pytest.mark.parametrize("flags", [0, hwc.FLAG_HORNER], ids=["auto", "horner"])
+@pytest.mark.parametrize("flags", [0, hwc.FLAG_FAN1, hwc.FLAG_HORNER], ids=["auto", "fan1", "horner"])
 def test_character_sum_identity_on_gpu(g, q, d, flags):
     """Unfiltered whole MZ_d family: sum_f sum_x chi(f(x)) = sum over m | k with
     k/m even of N_m q^(d-1-m) (q^m - 1) (N_m = elements of degree exactly m)."""
