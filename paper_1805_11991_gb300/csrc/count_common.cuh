@@ -221,7 +221,7 @@ __device__ void stage_job(const KJob &J, uint8_t *smem)
         const uint32_t *src = J.coef_log[k];
         uint32_t *dst = s32 + J.coef_off[k];
         for (uint32_t i = threadIdx.x; i < J.q; i += blockDim.x) dst[i] = src[i];
-        if (J.method == 1) {
+        if (J.method != 0) {
             const uint32_t nw = J.L[k] * J.words;
             const uint32_t *rs = reinterpret_cast<const uint32_t *>(J.rows[k]);
             uint32_t *rd = reinterpret_cast<uint32_t *>(smem + J.row_off[k]);
@@ -230,7 +230,7 @@ __device__ void stage_job(const KJob &J, uint8_t *smem)
             for (uint32_t i = threadIdx.x; i + 1 < J.q; i += blockDim.x) zd[i] = J.zdig[k][i];
         }
     }
-    if (J.method == 1) {   // F_q digit arithmetic: mul | sub | inv
+    if (J.method != 0) {   // F_q digit arithmetic: mul | sub | inv
         const uint32_t qq = J.q * J.q;
         uint8_t *d = smem + J.fq_off;
         for (uint32_t i = threadIdx.x; i < qq; i += blockDim.x) {
