@@ -128,6 +128,99 @@ __device__ __forceinline__ void group2_field(const TabS T, const KJob &J, int k,
     if (role && n0) atomicAdd(&n0s[b], n0);
 }
 
+// Square-freeness of the q members f_c = g_b + c (c in F_q) that share
+// g_b(x) = u(x) + b x.  They share f' = w = u' + b, and gcd(f_c, w) != 1 exactly
+// when some root theta of w has g_b(theta) = -c.  The characteristic polynomial
+// of multiplication by g_b on F_q[x]/(w) is prod_theta (t - g_b(theta)) over the
+// roots of w with multiplicity, so f_c is square-free iff chi(-c) != 0 (for
+// deg w >= 1; w = 0 means f' = 0, never square-free; w a nonzero constant
+// means always square-free).  chi comes from a Hessenberg form (similarity
+// transforms) and the Hessenberg recurrence.  F_q arithmetic on digits with
+// the mul / sub / inv tables.  Returns the mask of square-free c (bit c).
+template <int D>
+__device__ __noinline__ uint32_t sqf_mask_for_b(const uint8_t *mulT, const uint8_t *subT, const uint8_t *invT,
+                                                uint32_t q, uint32_t p, const uint32_t *cg, uint32_t b)
+{
+    constexpr int MX = D - 1;   // deg w <= D - 1
+    auto mul = [&](uint32_t x, uint32_t y) -> uint32_t { return mulT[x * q + y]; };
+    auto sub = [&](uint32_t x, uint32_t y) -> uint32_t { return subT[x * q + y]; };
+    auto add = [&](uint32_t x, uint32_t y) -> uint32_t { return subT[x * q + subT[y]]; };   // x - (0 - y)
+    const uint32_t all = (q >= 32) ? 0xFFFFFFFFu : ((1u << q) - 1u);
+    // w = f' = b + sum_{i>=2} (i mod p) c_i x^(i-1)
+    uint32_t w[MX + 1];
+    w[0] = b;
+    for (int i = 2; i <= D; ++i) w[i - 1] = mul(i % p, cg[i]);
+    int m = MX;
+    while (m >= 0 && w[m] == 0) --m;
+    if (m < 0) return 0u;
+    if (m == 0) return all;
+    const uint32_t wi = invT[w[m]];
+    for (int i = 0; i <= m; ++i) w[i] = mul(w[i], wi);   // monic
+    // r = g_b mod w, g_b = b x + sum_{i>=2} c_i x^i
+    uint32_t r[D + 1];
+    r[0] = 0;
+    r[1] = b;
+    for (int i = 2; i <= D; ++i) r[i] = cg[i];
+    for (int t = D; t >= m; --t) {
+        const uint32_t cf = r[t];
+        if (!cf) continue;
+        r[t] = 0;
+        for (int i = 0; i < m; ++i) r[t - m + i] = sub(r[t - m + i], mul(cf, w[i]));
+    }
+    // H[i][j]: coefficient i of g_b x^j mod w
+    uint32_t H[MX][MX];
+    for (int j = 0; j < m; ++j) {
+        for (int i = 0; i < m; ++i) H[i][j] = r[i];
+        const uint32_t top = r[m - 1];
+        for (int i = m - 1; i >= 1; --i) r[i] = sub(r[i - 1], mul(top, w[i]));
+        r[0] = sub(0, mul(top, w[0]));
+    }
+    // upper Hessenberg form by similarity
+    for (int j = 0; j + 2 < m; ++j) {
+        int piv = -1;
+        for (int i = j + 1; i < m; ++i)
+            if (H[i][j]) { piv = i; break; }
+        if (piv < 0) continue;
+        if (piv != j + 1) {
+            for (int k = 0; k < m; ++k) { const uint32_t t = H[piv][k]; H[piv][k] = H[j + 1][k]; H[j + 1][k] = t; }
+            for (int k = 0; k < m; ++k) { const uint32_t t = H[k][piv]; H[k][piv] = H[k][j + 1]; H[k][j + 1] = t; }
+        }
+        const uint32_t iv = invT[H[j + 1][j]];
+        for (int i = j + 2; i < m; ++i) {
+            if (!H[i][j]) continue;
+            const uint32_t f = mul(H[i][j], iv);
+            for (int k = 0; k < m; ++k) H[i][k] = sub(H[i][k], mul(f, H[j + 1][k]));
+            for (int k = 0; k < m; ++k) H[k][j + 1] = add(H[k][j + 1], mul(f, H[k][i]));
+        }
+    }
+    // p_k(t) = (t - h_kk) p_{k-1} - sum_{i<k} h_ik (prod_{j=i+1..k} h_{j,j-1}) p_{i-1}  (1-based)
+    uint32_t P[MX + 1][MX + 1];
+    P[0][0] = 1;
+    for (int k = 1; k <= m; ++k) {
+        for (int e = 0; e <= k; ++e) {   // (t - h_kk) p_{k-1}
+            uint32_t v = (e >= 1) ? P[k - 1][e - 1] : 0u;
+            if (e <= k - 1) v = sub(v, mul(H[k - 1][k - 1], P[k - 1][e]));
+            P[k][e] = v;
+        }
+        uint32_t prod = 1;
+        for (int i = k - 1; i >= 1; --i) {
+            prod = mul(prod, H[i][i - 1]);            // h_{i+1,i} (1-based)
+            const uint32_t f = mul(H[i - 1][k - 1], prod);
+            if (!f) continue;
+            for (int e = 0; e <= i - 1; ++e) P[k][e] = sub(P[k][e], mul(f, P[i - 1][e]));
+        }
+    }
+    // member c square-free iff chi(-c) != 0
+    uint32_t mask = 0;
+    for (uint32_t c = 0; c < q; ++c) {
+        const uint32_t t = sub(0, c);
+        uint32_t v = P[m][m];
+        for (int e = m - 1; e >= 0; --e) v = add(mul(v, t), P[m][e]);
+        if (v) mask |= 1u << c;
+    }
+    return mask;
+}
+
 // one group of q^2 members (c_1, c_0 free) for one warp
 template <int D>
 __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, const uint8_t *smem,
@@ -159,31 +252,37 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
     const uint8_t *subT = mulT + qq;
     const uint8_t *invT = subT + qq;
 
-    // square-freeness of the q^2 members, 32 at a time
+    // square-freeness: lane b settles the q members with c_1 = b at once
+    for (uint32_t t = lane; t < nw; t += 32) sqfw[t] = 0;
+    for (uint32_t m = lane; m < qq; m += 32) keys[m] = 0;
+    __syncwarp();
+    if ((uint32_t)lane < q) {
+        const uint32_t mask = sqf_mask_for_b<D>(mulT, subT, invT, q, J.p, c, (uint32_t)lane);
+        // bits b*q .. b*q + q-1 of the member mask
+        const uint32_t bit0 = (uint32_t)lane * q;
+        const uint32_t w0 = bit0 >> 5, sh = bit0 & 31u;
+        if (mask) {
+            atomicOr(&sqfw[w0], mask << sh);
+            if (sh && sh + q > 32) atomicOr(&sqfw[w0 + 1], mask >> (32 - sh));
+        }
+    }
+    __syncwarp();
     uint32_t anyv = 0, anys = 0;
     for (uint32_t t = 0; t < nw; ++t) {
         const uint32_t m = t * 32 + lane;
         const uint64_t idx = base + m;
         const bool v = m < qq && idx >= J.first && idx < J.first + J.count;
-        bool sq = false;
-        if (v) {
-            uint32_t cm[D + 1];
-#pragma unroll
-            for (int i = 0; i <= D; ++i) cm[i] = c[i];
-            cm[0] = m % q;
-            cm[1] = m / q;
-            sq = squarefree_digits<D>(mulT, subT, invT, q, J.p, cm);
-        }
+        const bool sq = v && ((sqfw[t] >> lane) & 1u);
         const unsigned vm = __ballot_sync(0xFFFFFFFFu, v);
         const unsigned sm = __ballot_sync(0xFFFFFFFFu, sq);
+        __syncwarp();
         if (lane == 0) {
-            sqfw[t] = sm;
+            sqfw[t] = sm;   // square-free and in range
             st.examined += __popc(vm);
             st.sqf += __popc(sm);
         }
         anyv |= vm;
         anys |= sm;
-        if (m < qq) keys[m] = 0;
     }
     __syncwarp();
     if ((J.unfiltered ? anyv : anys) == 0) {
