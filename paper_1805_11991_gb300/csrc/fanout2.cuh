@@ -78,6 +78,7 @@ __device__ __forceinline__ void group2_field(const TabS T, const KJob &J, int k,
     const uint32_t zdiv = J.zdiv[k];
     const uint32_t *coefk = reinterpret_cast<const uint32_t *>(smem) + J.coef_off[k];
     const uint32_t lam_b = (role && b != 0) ? coefk[b] : L;
+    const uint32_t lam0 = lam_b == L ? 0u : lam_b;   // log b (b = 0: unused)
     uint32_t *acc_b = acc + b * q;
     uint32_t P[kFan2Planes];
 #pragma unroll
@@ -94,29 +95,40 @@ __device__ __forceinline__ void group2_field(const TabS T, const KJob &J, int k,
         const uint32_t nb = min(64u, L - j0);              // points in this batch
         const uint32_t T_in = (nb + S - 1) / S;            // inputs per lane (uniform)
         for (uint32_t t0 = 0; t0 < T_in; t0 += 8) {
-            uint32_t a[8];
+            // phases over 8 inputs, so that the 8 dependent lookup pairs overlap:
+            // staged u -> Zech step -> row; the rare zero-digit updates come last
+            uint32_t a[8], ly[8], lbx[8], okm = 0;
 #pragma unroll
             for (int v = 0; v < 8; ++v) {
                 const uint32_t i = s + (t0 + v) * S;
                 const bool ok = role && i < nb;
-                const uint32_t U = Us[ok ? i : 0];
-                const uint32_t xi = j0 + i;
-                // y_b = u + b x: Zech addition in the log domain
-                const uint32_t lbx = addmod(lam_b == L ? 0u : lam_b, ok ? xi : 0u, L);
-                const uint32_t n = U + (L - lbx);            // in [1, 2L]
-                const uint32_t z = T[n];
-                uint32_t ly;
-                if (b == 0) ly = U;                          // y_0 = u
-                else if (U >= L) ly = lbx;                   // u = 0: y = b x
-                else ly = (z >= cap) ? L : addmod(lbx, z, L);
-                const bool zero = ly >= L;
-                const uint32_t r = rows[zero ? 0 : ly];
+                okm |= (ok ? 1u : 0u) << v;
+                ly[v] = Us[ok ? i : 0];
+                lbx[v] = addmod(lam0, j0 + (ok ? i : 0u), L);
+            }
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+                // y_b = u + b x: Zech addition in the log domain, n in [1, 2L]
+                const uint32_t U = ly[v];
+                const uint32_t z = T[U + (L - lbx[v])];
+                if (b != 0) ly[v] = (U >= L) ? lbx[v] : ((z >= cap) ? L : addmod(lbx[v], z, L));
+            }
+            uint32_t rare = 0;
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+                const bool ok = (okm >> v) & 1u;
+                const bool zero = ly[v] >= L;
+                const uint32_t r = rows[zero ? 0 : ly[v]];
                 a[v] = (ok && !zero) ? (r & 0x7FFFFFFFu) : 0u;
                 n0 += (ok && zero) ? 1u : 0u;
-                if (ok && !zero && (r >> 31))   // y in F_q^x: y + c = 0 for one digit c
-                    atomicAdd(&acc_b[zdig[zdiv ? __umulhi(ly, zdiv) : ly]], 1u);
+                rare |= ((ok && !zero && (r >> 31)) ? 1u : 0u) << v;   // y in F_q^x: y + c = 0 for one c
             }
             add8_p10(P, a);
+            if (rare) {
+#pragma unroll
+                for (int v = 0; v < 8; ++v)
+                    if ((rare >> v) & 1u) atomicAdd(&acc_b[zdig[zdiv ? __umulhi(ly[v], zdiv) : ly[v]]], 1u);
+            }
             if (++nblk == kFan2FlushBlocks) {
                 flush_planes(P, acc_b, q, role);
                 nblk = 0;
@@ -237,14 +249,15 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
 #pragma unroll
     for (int i = 2; i < D; ++i) nz |= (c[i] != 0 ? 1u : 0u) << i;
 
-    // per-warp scratch: Us[64] | acc[q^2] | n0s[q] | sqf[ceil(q^2/32)] | keys[q^2] (u64)
+    // per-warp shared scratch: Us[64] | acc[q^2] | n0s[q] | sqf[ceil(q^2/32)];
+    // the members' keys live in this warp's slot of global scratch
     uint32_t *Us = reinterpret_cast<uint32_t *>(wsm);
     uint32_t *acc = Us + 64;
     uint32_t *n0s = acc + qq;
     uint32_t *sqfw = n0s + q;
     const uint32_t nw = (qq + 31) / 32;
     unsigned long long *keys =
-        reinterpret_cast<unsigned long long *>(wsm + ((4u * (64 + qq + q + nw) + 7u) & ~7u));
+        J.wkeys + ((uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * J.wkeys_stride;
 
     const uint16_t *s16 = reinterpret_cast<const uint16_t *>(smem);
     const uint32_t *s32 = reinterpret_cast<const uint32_t *>(smem);
@@ -346,6 +359,7 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
         __syncwarp();
     }
     if (J.member_counts) return;
+    __syncwarp();
     for (uint32_t t = 0; t < nw; ++t) {
         const uint32_t m = t * 32 + lane;
         const bool sq = m < qq && ((sqfw[t] >> lane) & 1u);
@@ -360,7 +374,7 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
 }
 
 template <int D>
-__global__ void __launch_bounds__(kFan2Warps * 32, 4)
+__global__ void __launch_bounds__(512, 1)
     k_fan2_persistent(const KJob *__restrict__ jobs, const uint64_t *__restrict__ item_start, uint32_t n_jobs,
                       uint64_t n_items, unsigned long long *counter, uint32_t item_tiles)
 {

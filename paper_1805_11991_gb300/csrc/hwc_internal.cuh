@@ -114,6 +114,8 @@ struct KJob {
     uint32_t zdig_off[kMaxG];         // byte offset of zdig in smem
     uint32_t zdiv[kMaxG];             // ceil(2^32 / (L/(q-1))): l / s by a high multiply
     uint32_t warp_off, warp_bytes;    // per-warp scratch in smem (method 2)
+    unsigned long long *wkeys;        // per-warp member keys in global memory (method 2):
+    uint32_t wkeys_stride, pad3;      //   slot blockIdx.x * warps + warp, stride q^2
     const uint8_t *fq_mul, *fq_sub, *fq_inv;   // digit arithmetic of F_q (fan-out jobs)
     uint32_t fq_off;                  // byte offset of mul | sub | inv in smem
     // outputs
@@ -172,14 +174,20 @@ const void *fan2_kernel(int D);
 const void *fan2_kernel_a(int D);   // fan2_a.cu, D = 3..6
 const void *fan2_kernel_b(int D);   // fan2_b.cu, D = 7..10
 constexpr int kFan2WarpsHost = 4;   // warps per CTA of the two-level kernel
-// per-warp scratch bytes of the two-level kernel for q
+// per-warp shared scratch bytes of the two-level kernel for q:
+// U[64] | acc[q^2] | n0[q] | square-free bits[ceil(q^2/32)]
 inline uint32_t fan2_warp_bytes(uint32_t q)
 {
     const uint32_t qq = q * q, nw = (qq + 31) / 32;
-    uint32_t b = (4u * (64 + qq + q + nw) + 7u) & ~7u;
-    b += 8u * qq;
-    return (b + 15u) & ~15u;
+    return (4u * (64 + qq + q + nw) + 15u) & ~15u;
 }
+// launch shape of the two-level kernel for jobs with these smem needs: the
+// block (4, 8 or 16 warps) that keeps most warps resident; *smem receives the
+// dynamic shared memory of that block
+struct Fan2Need {
+    uint32_t warp_off, warp_bytes;
+};
+int choose_shape_fan2(int D, const Fan2Need *needs, size_t n, LaunchShape *out, uint32_t *smem);
 const void *fan_kernel_e(int D, int W, bool persistent);   // fanout_e.cu, D = 9, 10
 // hash slots for a job of `count` members (power of two)
 uint32_t hash_capacity(uint32_t g, uint32_t q, uint64_t count, uint32_t scale);

@@ -111,7 +111,7 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit)
         uint64_t b = 0;
         for (uint32_t k = 0; k < j.g; ++k) b += 4ull * j.words * j.L[k] + ((j.q + 15) / 16) * 16;
         b += ((2ull * j.q * j.q + j.q + 15) / 16) * 16;
-        if (j.method == 2) b += 16 + (uint64_t)kFan2WarpsHost * fan2_warp_bytes(j.q);
+        if (j.method == 2) b += 16 + (uint64_t)kFan2WarpsHost * fan2_warp_bytes(j.q);   // smallest block
         return b;
     };
     auto bytes_for = [&](void) {
@@ -119,6 +119,18 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit)
         for (uint32_t k = 0; k < j.g; ++k) u16 += words(k);
         return u16 * 2 + 4ull * j.g * ((j.q + 3) / 4) * 4 + fan_bytes();
     };
+    // the two-level kernel reads its Zech tables only in the shared chain: give
+    // up tripled tables, largest first, while that makes room for 16 warps
+    if (j.method == 2) {
+        const uint64_t extra = (uint64_t)(16 - kFan2WarpsHost) * fan2_warp_bytes(j.q);
+        while (bytes_for() + extra > smem_limit) {
+            int big = -1;
+            for (uint32_t k = 0; k < j.g; ++k)
+                if (kind[k] == kTabTripleSmem && j.zech2[k] && (big < 0 || words(k) > words(big))) big = (int)k;
+            if (big < 0) break;
+            kind[big] = kTabDoubleSmem;
+        }
+    }
     while (bytes_for() > smem_limit) {
         int big = -1;
         for (uint32_t k = 0; k < j.g; ++k)
@@ -434,6 +446,31 @@ int hwc::choose_shape(int D, uint32_t method, uint32_t words, uint32_t smem, boo
     return HWC_OK;
 }
 
+int hwc::choose_shape_fan2(int D, const Fan2Need *needs, size_t n, LaunchShape *out, uint32_t *smem)
+{
+    const int sms = device_sm_count();
+    const uint32_t limit = device_smem_optin() - 4096;
+    int best_warps = -1;
+    for (int block : {512, 256, 128}) {
+        const uint32_t W = (uint32_t)block / 32;
+        uint32_t need = 0;
+        for (size_t i = 0; i < n; ++i) need = std::max(need, needs[i].warp_off + W * needs[i].warp_bytes);
+        if (need > limit) continue;
+        int ctas = 0;
+        int rc = max_ctas_per_sm(D, 2, 1, block, need, true, &ctas);
+        if (rc) return rc;
+        if (ctas * (int)W > best_warps) {
+            best_warps = ctas * (int)W;
+            out->block = block;
+            out->grid = sms * ctas;
+            out->item_tiles = (int)W;
+            *smem = need;
+        }
+    }
+    if (best_warps <= 0) return set_error(HWC_ERR_TOO_LARGE, "no CTA of the two-level kernel fits");
+    return HWC_OK;
+}
+
 static int batch_create_impl(const hwc_job_t *jobs, size_t n, uint32_t flags, uint32_t cap_scale,
                              hwc_batch **out)
 {
@@ -497,7 +534,28 @@ static int batch_create_impl(const hwc_job_t *jobs, size_t n, uint32_t flags, ui
     const bool persistent = !(flags & HWC_FLAG_PLAIN);
     std::vector<uint64_t> starts;
     for (BatchGroup &G : b->groups) {
-        if ((rc = choose_shape(G.D, G.method, G.words, G.max_smem, persistent, &G.shape))) {
+        if (G.method == 2) {
+            std::vector<Fan2Need> needs;
+            uint32_t max_qq = 0;
+            for (uint32_t r = G.first; r < G.first + G.n; ++r) {
+                needs.push_back({b->jobs[r].kj.warp_off, b->jobs[r].kj.warp_bytes});
+                max_qq = std::max(max_qq, b->jobs[r].kj.q * b->jobs[r].kj.q);
+            }
+            if ((rc = choose_shape_fan2(G.D, needs.data(), needs.size(), &G.shape, &G.max_smem))) {
+                batch_release(b);
+                return rc;
+            }
+            // one key slot per resident warp of the launch
+            unsigned long long *wk = nullptr;
+            if ((rc = dalloc(b, &wk, (uint64_t)G.shape.grid * (G.shape.block / 32) * max_qq))) {
+                batch_release(b);
+                return rc;
+            }
+            for (uint32_t r = G.first; r < G.first + G.n; ++r) {
+                b->jobs[r].kj.wkeys = wk;
+                b->jobs[r].kj.wkeys_stride = max_qq;
+            }
+        } else if ((rc = choose_shape(G.D, G.method, G.words, G.max_smem, persistent, &G.shape))) {
             batch_release(b);
             return rc;
         }
@@ -717,7 +775,17 @@ extern "C" int hwc_count_members(uint32_t g, uint32_t q, const hwc_family_t *fam
     cudaStream_t s = (cudaStream_t)stream;
     hwc_batch *b = new hwc_batch();   // allocation holder only
     LaunchShape sh;
-    rc = choose_shape((int)kj.d, kj.method, kj.words, kj.smem_bytes, true, &sh);
+    uint32_t launch_smem = kj.smem_bytes;
+    if (kj.method == 2) {
+        const Fan2Need need{kj.warp_off, kj.warp_bytes};
+        rc = choose_shape_fan2((int)kj.d, &need, 1, &sh, &launch_smem);
+        if (rc == HWC_OK) {
+            rc = dalloc(b, &kj.wkeys, (uint64_t)sh.grid * (sh.block / 32) * kj.q * kj.q);
+            kj.wkeys_stride = kj.q * kj.q;
+        }
+    } else {
+        rc = choose_shape((int)kj.d, kj.method, kj.words, kj.smem_bytes, true, &sh);
+    }
     uint64_t starts[2] = {0, 0};
     starts[1] = (kj.n_tiles + sh.item_tiles - 1) / sh.item_tiles;
     if (rc == HWC_OK &&
@@ -740,7 +808,7 @@ extern "C" int hwc_count_members(uint32_t g, uint32_t q, const hwc_family_t *fam
         return set_error(HWC_ERR_CUDA, "setup: %s", cudaGetErrorString(ce));
     }
     rc = launch_persistent((int)kj.d, kj.method, kj.words, b->d_jobs, b->d_item_start, 1, starts[1],
-                           b->d_counters, kj.smem_bytes, sh, s);
+                           b->d_counters, launch_smem, sh, s);
     if (rc == HWC_OK) {
         ce = cudaMemcpyAsync(counts, kj.member_counts, count * g * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
         if (ce == cudaSuccess) ce = cudaMemcpyAsync(sqf, kj.member_sqf, count, cudaMemcpyDeviceToHost, s);

@@ -62,6 +62,8 @@ struct hwc_server {
     KJob *h_jobs = nullptr;          // pinned staging
     uint64_t *h_item_start = nullptr;
     std::map<std::pair<int, uint32_t>, LaunchShape> shapes;
+    unsigned long long *d_wkeys = nullptr;   // two-level kernel: member keys per resident warp
+    uint64_t wkeys_slots = 0;
     uint64_t steps = 0;
 };
 
@@ -216,7 +218,16 @@ void server_loop(hwc_server *s)
             while (e < n && skey(step[e]) == skey(step[i])) smem = std::max(smem, step[e++]->kj.smem_bytes);
             StepGroup G{(int)step[i]->kj.d, step[i]->kj.method, step[i]->kj.words, i, e - i, item_off, 0, smem,
                         LaunchShape()};
-            rc = shape_for(s, G.D, G.method, G.words, smem, &G.sh);
+            if (G.method == 2) {
+                std::vector<Fan2Need> needs;
+                for (uint32_t r = i; r < e; ++r) needs.push_back({step[r]->kj.warp_off, step[r]->kj.warp_bytes});
+                rc = choose_shape_fan2(G.D, needs.data(), needs.size(), &G.sh, &G.smem);
+                if (rc == HWC_OK &&
+                    (uint64_t)G.sh.grid * (G.sh.block / 32) * 961ull > s->wkeys_slots)
+                    rc = set_error(HWC_ERR_TOO_LARGE, "server key scratch too small");
+            } else {
+                rc = shape_for(s, G.D, G.method, G.words, smem, &G.sh);
+            }
             if (rc) break;
             uint64_t budget = s->cfg.step_items ? s->cfg.step_items : (uint64_t)G.sh.grid * 4;
             budget *= (uint64_t)G.sh.item_tiles;
@@ -236,6 +247,8 @@ void server_loop(hwc_server *s)
                     sl.count = std::min<uint64_t>(q->kj.count - q->next_tile * kTileMembers, t * kTileMembers);
                 }
                 sl.n_tiles = t;
+                sl.wkeys = s->d_wkeys;
+                sl.wkeys_stride = 961;   // q <= 31
                 s->h_jobs[r] = sl;
                 s->h_item_start[item_off + (r - i)] = items;
                 items += (t + G.sh.item_tiles - 1) / G.sh.item_tiles;
@@ -308,6 +321,9 @@ extern "C" int hwc_serve_open(const hwc_server_config_t *cfg, hwc_server_t **out
               cudaMalloc(&s->d_counters, m * sizeof(unsigned long long)) == cudaSuccess &&
               cudaMallocHost(&s->h_jobs, m * sizeof(KJob)) == cudaSuccess &&
               cudaMallocHost(&s->h_item_start, 2 * (m + 1) * sizeof(uint64_t)) == cudaSuccess;
+    // every resident warp of the GPU (at most 64 per SM) may hold q^2 <= 961 keys
+    s->wkeys_slots = (uint64_t)device_sm_count() * 64 * 961;
+    ok = ok && cudaMalloc(&s->d_wkeys, s->wkeys_slots * sizeof(unsigned long long)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         hwc_serve_close(s);
@@ -398,6 +414,7 @@ extern "C" int hwc_serve_close(hwc_server_t *s)
     cudaFree(s->d_jobs);
     cudaFree(s->d_item_start);
     cudaFree(s->d_counters);
+    cudaFree(s->d_wkeys);
     if (s->h_jobs) cudaFreeHost(s->h_jobs);
     if (s->h_item_start) cudaFreeHost(s->h_item_start);
     if (s->stream) cudaStreamDestroy(s->stream);
