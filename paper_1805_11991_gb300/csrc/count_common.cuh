@@ -13,6 +13,11 @@ struct TabS {   // u16 table in shared memory
     const uint16_t *t;
     __device__ __forceinline__ uint32_t operator[](uint32_t u) const { return t[u]; }
 };
+template <bool PAD>
+struct TabP {   // u16 table in shared memory; PAD: entry i at i + 2 floor(i / 64)
+    const uint16_t *t;
+    __device__ __forceinline__ uint32_t operator[](uint32_t u) const { return PAD ? t[u + ((u >> 6) << 1)] : t[u]; }
+};
 struct TabG {   // u32 table in global memory (L1/L2 resident)
     const uint32_t *t;
     __device__ __forceinline__ uint32_t operator[](uint32_t u) const { return __ldg(t + u); }
@@ -216,18 +221,21 @@ __device__ void stage_job(const KJob &J, uint8_t *smem)
             const uint32_t n = (tri ? 3 : 2) * J.L[k] + 1;
             const uint16_t *src = tri ? J.zech3[k] : J.zech2[k];
             uint16_t *dst = s16 + J.tab_off[k];
-            for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+            if (J.tab_pad[k])   // entry i at i + 2 floor(i / 64)
+                for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) dst[i + ((i >> 6) << 1)] = src[i];
+            else
+                for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
         }
         const uint32_t *src = J.coef_log[k];
         uint32_t *dst = s32 + J.coef_off[k];
         for (uint32_t i = threadIdx.x; i < J.q; i += blockDim.x) dst[i] = src[i];
         if (J.method != 0) {
-            const uint32_t nw = J.L[k] * J.words;
+            const uint32_t nw = (J.L[k] + 1) * J.words;   // row L: y = 0
             const uint32_t *rs = reinterpret_cast<const uint32_t *>(J.rows[k]);
             uint32_t *rd = reinterpret_cast<uint32_t *>(smem + J.row_off[k]);
             for (uint32_t i = threadIdx.x; i < nw; i += blockDim.x) rd[i] = rs[i];
             uint8_t *zd = smem + J.zdig_off[k];
-            for (uint32_t i = threadIdx.x; i + 1 < J.q; i += blockDim.x) zd[i] = J.zdig[k][i];
+            for (uint32_t i = threadIdx.x; i < J.q; i += blockDim.x) zd[i] = J.zdig[k][i];
         }
     }
     if (J.method != 0) {   // F_q digit arithmetic: mul | sub | inv

@@ -24,7 +24,7 @@
 namespace hwc {
 namespace {
 
-constexpr int kFan2Warps = 4;                 // warps per CTA
+constexpr int kFan2Warps = 4;                 // smallest block (warps)
 constexpr int kFan2Planes = 10;               // per-lane counts < 1024 between flushes
 constexpr uint32_t kFan2FlushBlocks = 127;    // 8-input blocks per lane between flushes
 
@@ -47,97 +47,141 @@ __device__ __forceinline__ void add8_p10(uint32_t (&P)[kFan2Planes], const uint3
     }
 }
 
-// add the per-position counts of the planes into acc[c] (2 per row bit), clear
-__device__ __forceinline__ void flush_planes(uint32_t (&P)[kFan2Planes], uint32_t *acc_b, uint32_t q,
-                                             bool role)
+// add the per-position counts of the planes into the lane's row (2 per row
+// bit), clear the planes
+__device__ __forceinline__ void flush_planes(uint32_t (&P)[kFan2Planes], uint16_t *acc_row, uint32_t q, bool role)
 {
     if (role) {
         for (uint32_t c = 0; c < q; ++c) {
             uint32_t v = 0;
 #pragma unroll
             for (int b = 0; b < kFan2Planes; ++b) v |= ((P[b] >> c) & 1u) << b;
-            if (v) atomicAdd(&acc_b[c], 2 * v);
+            if (v) acc_row[c] = (uint16_t)(acc_row[c] + 2 * v);
         }
     }
 #pragma unroll
     for (int b = 0; b < kFan2Planes; ++b) P[b] = 0;
 }
 
-// points of one field for the whole group (all q^2 members), lane role (b, s)
-template <int D, bool TRIPLE>
-__device__ __forceinline__ void group2_field(const TabS T, const KJob &J, int k, const uint8_t *smem,
-                                             const HChain<D> &H, const uint32_t (&lam)[D + 1], uint32_t nz,
-                                             uint32_t *Us, uint32_t *acc, uint32_t *n0s, int lane, bool role,
-                                             uint32_t b, uint32_t s, uint32_t S)
+// the lane's queued points with y in F_q (y + c = 0 for one digit c): z(b, c) += 1
+__device__ __forceinline__ void drain_queue(const uint16_t *rq, uint32_t qn, int lane, const uint8_t *zdig,
+                                            uint32_t zdiv, uint16_t *acc_row)
 {
-    const uint32_t L = J.L[k], q = J.q;
-    const uint32_t cap = TRIPLE ? 3 * L : 2 * L;
+    for (uint32_t i = 0; i < qn; ++i) {
+        const uint32_t l = rq[i * 32 + lane];
+        const uint32_t d = zdig[zdiv ? __umulhi(l, zdiv) : l];
+        acc_row[d] = (uint16_t)(acc_row[d] + 1);
+    }
+}
+
+// One block of 8 consecutive points x = alpha^(j0 + i), i = i0 + t0 .. + 7,
+// for lane (b, s).  Phases over the 8 points so that their lookups overlap:
+// staged log u -> Zech addition y_b = u + b x (eq. 2.1) -> fan-out row of
+// y_b.  The row of y_b carries bit c = [chi(y_b + c) = -1] and a flag for
+// y_b in F_q (y_b = 0 included: row L), whose zero digit goes to the queue.
+// GEN: some points of the block may be missing (okm) or have u = 0.
+template <bool GEN, class Tab>
+__device__ __forceinline__ void fan2_block(const Tab T, const uint32_t *__restrict__ rows, const uint32_t *Us,
+                                           uint32_t L, uint32_t &lbx, bool b0, bool role, uint32_t okm,
+                                           uint16_t *rq, int lane, uint32_t &qn, uint32_t (&a)[8])
+{
+    const uint4 w0 = *reinterpret_cast<const uint4 *>(Us);
+    const uint4 w1 = *reinterpret_cast<const uint4 *>(Us + 4);
+    const uint32_t U[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+    uint32_t ly[8];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        // log(u + b x) = log(b x) + Z(log u - log(b x)); index in [1, 2L] for u != 0
+        const uint32_t z = T[U[v] + (L - lbx)];
+        uint32_t t = lbx + z;            // < 2L, or >= 2L when u + b x = 0 (z poisoned)
+        t = min(t, t - L);               // mod L; the poisoned case stays >= L
+        t = min(t, L);                   // row L: y = 0
+        if (GEN) t = (U[v] >= L) ? lbx : t;   // u = 0: y = b x
+        ly[v] = b0 ? U[v] : t;           // b = 0: y = u
+        lbx = (lbx + 1 == L) ? 0u : lbx + 1;
+    }
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        const uint32_t r = rows[ly[v]];
+        const bool ok = GEN ? ((okm >> v) & 1u) != 0 : role;
+        a[v] = (!GEN || ok) ? (r & 0x7FFFFFFFu) : 0u;
+        rq[qn * 32 + lane] = (uint16_t)ly[v];   // kept when the flag is set
+        qn += (ok && (r >> 31)) ? 1u : 0u;
+    }
+}
+
+// points of one field for the whole group (all q^2 members), lane role (b, s)
+template <int D, bool TRIPLE, bool PAD>
+__device__ __forceinline__ void group2_field(const KJob &J, int k, const uint8_t *smem, const HChain<D> &H,
+                                             const uint32_t (&lam)[D + 1], uint32_t nz, uint32_t *Us,
+                                             uint16_t *acc_row, uint16_t *rq, int lane, bool role, uint32_t b,
+                                             uint32_t s, uint32_t S)
+{
+    const TabP<PAD> T{reinterpret_cast<const uint16_t *>(smem) + J.tab_off[k]};
+    const uint32_t L = J.L[k];
     const uint32_t bar = J.barrett[k];
-    const uint32_t *rows = reinterpret_cast<const uint32_t *>(smem + J.row_off[k]);
+    const uint32_t *rows = reinterpret_cast<const uint32_t *>(smem + J.row_off[k]);   // [L + 1]
     const uint8_t *zdig = smem + J.zdig_off[k];
     const uint32_t zdiv = J.zdiv[k];
     const uint32_t *coefk = reinterpret_cast<const uint32_t *>(smem) + J.coef_off[k];
-    const uint32_t lam_b = (role && b != 0) ? coefk[b] : L;
-    const uint32_t lam0 = lam_b == L ? 0u : lam_b;   // log b (b = 0: unused)
-    uint32_t *acc_b = acc + b * q;
+    const uint32_t lam_b = (b != 0) ? coefk[b] : 0u;   // log b
+    const bool b0 = b == 0;
+    const bool pow2S = S == 1 || S == 2 || S == 4 || S == 8;   // 64 / S points per lane, a multiple of 8
     uint32_t P[kFan2Planes];
 #pragma unroll
     for (int p = 0; p < kFan2Planes; ++p) P[p] = 0;
-    uint32_t nblk = 0, n0 = 0;
+    uint32_t nblk = 0, qn = 0;
     for (uint32_t j0 = 0; j0 < L; j0 += 64) {
         // log u(x) for the batch, two points per lane, staged for all lanes
         const uint32_t xA = j0 + lane, xB = j0 + 32 + lane;
         uint32_t uA, uB;
-        log_y_pair<D, TRIPLE, TabS, 2>(T, L, bar, H, lam, nz, xA < L ? xA : 0, xB < L ? xB : 0, uA, uB);
+        log_y_pair<D, TRIPLE, TabP<PAD>, 2>(T, L, bar, H, lam, nz, xA < L ? xA : 0, xB < L ? xB : 0, uA, uB);
         Us[lane] = uA;
         Us[32 + lane] = uB;
+        const bool uzero = __any_sync(0xFFFFFFFFu, uA >= L || uB >= L);
         __syncwarp();
-        const uint32_t nb = min(64u, L - j0);              // points in this batch
-        const uint32_t T_in = (nb + S - 1) / S;            // inputs per lane (uniform)
-        for (uint32_t t0 = 0; t0 < T_in; t0 += 8) {
-            // phases over 8 inputs, so that the 8 dependent lookup pairs overlap:
-            // staged u -> Zech step -> row; the rare zero-digit updates come last
-            uint32_t a[8], ly[8], lbx[8], okm = 0;
-#pragma unroll
-            for (int v = 0; v < 8; ++v) {
-                const uint32_t i = s + (t0 + v) * S;
-                const bool ok = role && i < nb;
-                okm |= (ok ? 1u : 0u) << v;
-                ly[v] = Us[ok ? i : 0];
-                lbx[v] = addmod(lam0, j0 + (ok ? i : 0u), L);
+        const uint32_t nb = min(64u, L - j0);   // points in this batch
+        if (pow2S && nb == 64 && !uzero) {
+            const uint32_t per = 64 / S, i0 = s * per;
+            uint32_t lbx = addmod(lam_b, j0 + i0, L);
+            for (uint32_t t0 = 0; t0 < per; t0 += 8) {
+                uint32_t a[8];
+                fan2_block<false>(T, rows, Us + i0 + t0, L, lbx, b0, role, 0u, rq, lane, qn, a);
+                add8_p10(P, a);
+                if (++nblk == kFan2FlushBlocks) {
+                    flush_planes(P, acc_row, J.q, role);
+                    nblk = 0;
+                }
+                if (__any_sync(0xFFFFFFFFu, qn > kFan2Queue - 8)) {
+                    drain_queue(rq, qn, lane, zdig, zdiv, acc_row);
+                    qn = 0;
+                }
             }
-#pragma unroll
-            for (int v = 0; v < 8; ++v) {
-                // y_b = u + b x: Zech addition in the log domain, n in [1, 2L]
-                const uint32_t U = ly[v];
-                const uint32_t z = T[U + (L - lbx[v])];
-                if (b != 0) ly[v] = (U >= L) ? lbx[v] : ((z >= cap) ? L : addmod(lbx[v], z, L));
-            }
-            uint32_t rare = 0;
-#pragma unroll
-            for (int v = 0; v < 8; ++v) {
-                const bool ok = (okm >> v) & 1u;
-                const bool zero = ly[v] >= L;
-                const uint32_t r = rows[zero ? 0 : ly[v]];
-                a[v] = (ok && !zero) ? (r & 0x7FFFFFFFu) : 0u;
-                n0 += (ok && zero) ? 1u : 0u;
-                rare |= ((ok && !zero && (r >> 31)) ? 1u : 0u) << v;   // y in F_q^x: y + c = 0 for one c
-            }
-            add8_p10(P, a);
-            if (rare) {
-#pragma unroll
-                for (int v = 0; v < 8; ++v)
-                    if ((rare >> v) & 1u) atomicAdd(&acc_b[zdig[zdiv ? __umulhi(ly[v], zdiv) : ly[v]]], 1u);
-            }
-            if (++nblk == kFan2FlushBlocks) {
-                flush_planes(P, acc_b, q, role);
-                nblk = 0;
+        } else {
+            // lane chunks of a multiple of 8 points; reads past 64 hit the
+            // zeroed slack of U and are masked
+            const uint32_t per = (((nb + S - 1) / S) + 7) & ~7u, i0 = s * per;
+            uint32_t lbx = addmod(lam_b, (j0 + i0) % L, L);
+            for (uint32_t t0 = 0; t0 < per; t0 += 8) {
+                const int nv = role ? min(8, max(0, (int)nb - (int)(i0 + t0))) : 0;
+                const uint32_t okm = (1u << nv) - 1u;
+                uint32_t a[8];
+                fan2_block<true>(T, rows, Us + i0 + t0, L, lbx, b0, role, okm, rq, lane, qn, a);
+                add8_p10(P, a);
+                if (++nblk == kFan2FlushBlocks) {
+                    flush_planes(P, acc_row, J.q, role);
+                    nblk = 0;
+                }
+                if (__any_sync(0xFFFFFFFFu, qn > kFan2Queue - 8)) {
+                    drain_queue(rq, qn, lane, zdig, zdiv, acc_row);
+                    qn = 0;
+                }
             }
         }
-        __syncwarp();   // Us is rewritten by the next batch
+        __syncwarp();   // U is rewritten by the next batch
     }
-    flush_planes(P, acc_b, q, role);
-    if (role && n0) atomicAdd(&n0s[b], n0);
+    flush_planes(P, acc_row, J.q, role);
+    drain_queue(rq, qn, lane, zdig, zdiv, acc_row);
 }
 
 // Square-freeness of the q members f_c = g_b + c (c in F_q) that share
@@ -249,12 +293,13 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
 #pragma unroll
     for (int i = 2; i < D; ++i) nz |= (c[i] != 0 ? 1u : 0u) << i;
 
-    // per-warp shared scratch: Us[64] | acc[q^2] | n0s[q] | sqf[ceil(q^2/32)];
-    // the members' keys live in this warp's slot of global scratch
+    // per-warp shared scratch (fan2_layout); the members' keys live in this
+    // warp's slot of global scratch
+    const Fan2Layout lay = fan2_layout(q);
     uint32_t *Us = reinterpret_cast<uint32_t *>(wsm);
-    uint32_t *acc = Us + 64;
-    uint32_t *n0s = acc + qq;
-    uint32_t *sqfw = n0s + q;
+    uint16_t *acc = reinterpret_cast<uint16_t *>(wsm + lay.acc_off);
+    uint16_t *rq = reinterpret_cast<uint16_t *>(wsm + lay.rq_off);
+    uint32_t *sqfw = reinterpret_cast<uint32_t *>(wsm + lay.sqf_off);
     const uint32_t nw = (qq + 31) / 32;
     unsigned long long *keys =
         J.wkeys + ((uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * J.wkeys_stride;
@@ -267,7 +312,7 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
 
     // square-freeness: lane b settles the q members with c_1 = b at once
     for (uint32_t t = lane; t < nw; t += 32) sqfw[t] = 0;
-    for (uint32_t m = lane; m < qq; m += 32) keys[m] = 0;
+    if (64 + (uint32_t)lane < lay.us) Us[64 + lane] = 0;   // slack read by 8-point blocks past 64
     __syncwarp();
     if ((uint32_t)lane < q) {
         const uint32_t mask = sqf_mask_for_b<D>(mulT, subT, invT, q, J.p, c, (uint32_t)lane);
@@ -311,11 +356,14 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
         return;
     }
 
-    // lane roles: S lanes per value b of c_1, each taking every S-th point
+    // lane roles: S lanes per value b of c_1, each taking a chunk of the points;
+    // lane = s q + b owns accumulator row `lane`
     const uint32_t S = 32 / q;
     const bool role = (uint32_t)lane < S * q;
     const uint32_t b = role ? (uint32_t)lane % q : 0;
     const uint32_t s = role ? (uint32_t)lane / q : 0;
+    uint16_t *acc_row = acc + (role ? (uint32_t)lane * q : 0u);
+    const uint32_t acc_words = (S * qq + 1) / 2;
 
 #pragma unroll 1
     for (int k = 0; k < G; ++k) {
@@ -326,35 +374,42 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
         for (int i = 0; i <= D; ++i) lam[i] = coefk[c[i]];
         HChain<D> H;
         make_hchain<D, 2>(H, lam, nz, L);
-        for (uint32_t m = lane; m < qq; m += 32) acc[m] = 0;
-        if ((uint32_t)lane < q) n0s[lane] = 0;
+        for (uint32_t m = lane; m < acc_words; m += 32) reinterpret_cast<uint32_t *>(acc)[m] = 0;
         __syncwarp();
-        if (J.tab_kind[k] == kTabTripleSmem)
-            group2_field<D, true>(TabS{s16 + J.tab_off[k]}, J, k, smem, H, lam, nz, Us, acc, n0s, lane, role, b,
-                                  s, S);
-        else
-            group2_field<D, false>(TabS{s16 + J.tab_off[k]}, J, k, smem, H, lam, nz, Us, acc, n0s, lane, role, b,
-                                   s, S);
+        const bool tri = J.tab_kind[k] == kTabTripleSmem;
+        if (J.tab_pad[k]) {
+            if (tri) group2_field<D, true, true>(J, k, smem, H, lam, nz, Us, acc_row, rq, lane, role, b, s, S);
+            else group2_field<D, false, true>(J, k, smem, H, lam, nz, Us, acc_row, rq, lane, role, b, s, S);
+        } else {
+            if (tri) group2_field<D, true, false>(J, k, smem, H, lam, nz, Us, acc_row, rq, lane, role, b, s, S);
+            else group2_field<D, false, false>(J, k, smem, H, lam, nz, Us, acc_row, rq, lane, role, b, s, S);
+        }
         __syncwarp();
+        // sum_x chi(f_{b,c}(x)) = (L - sum_s acc[s q + b][c]) + chi(c)   (x = 0: y = 0)
         int inf = 1;
         if (D == 2 * G + 2) inf += (lam[D] & 1u) ? -1 : 1;
-        for (uint32_t m = lane; m < qq; m += 32) {
-            const uint32_t bb = m / q, cc = m % q;
-            const uint32_t n0 = n0s[bb] + 1;                 // + x = 0 (y = 0)
+        if ((uint32_t)lane < q) {
+            const uint32_t cc = (uint32_t)lane;
             const uint32_t lc = coefk[cc];
             const int chi_c = (cc == 0) ? 0 : ((lc & 1u) ? -1 : 1);
-            const int S_ = (int)n0 * chi_c + (int)(Q - n0) - (int)acc[m];
-            const int N = (int)Q + S_ + inf;
-            if (J.member_counts) {
-                const uint64_t idx = base + m;
-                if (idx >= J.first && idx < J.first + J.count) {
-                    const bool sq = (sqfw[m / 32] >> (m % 32)) & 1u;
-                    J.member_counts[(idx - J.first) * G + k] = (sq || J.unfiltered) ? N : 0;
-                    if (k == 0) J.member_sqf[idx - J.first] = sq ? 1 : 0;
+            for (uint32_t bb = 0; bb < q; ++bb) {
+                const uint32_t m = bb * q + cc;
+                uint32_t tot = 0;
+                for (uint32_t ss = 0; ss < S; ++ss) tot += acc[(ss * q + bb) * q + cc];
+                const int N = (int)Q + ((int)L - (int)tot + chi_c) + inf;
+                if (J.member_counts) {
+                    const uint64_t idx = base + m;
+                    if (idx >= J.first && idx < J.first + J.count) {
+                        const bool sq = (sqfw[m / 32] >> (m % 32)) & 1u;
+                        J.member_counts[(idx - J.first) * G + k] = (sq || J.unfiltered) ? N : 0;
+                        if (k == 0) J.member_sqf[idx - J.first] = sq ? 1 : 0;
+                    }
                 }
+                const int a = (int)Q + 1 - N;   // eq. 1.1
+                const unsigned long long part = (unsigned long long)((uint32_t)(a + 32768) & 0xFFFFu) << (16 * k);
+                if (k == 0) keys[m] = part;
+                else keys[m] |= part;
             }
-            const int a = (int)Q + 1 - N;   // eq. 1.1
-            keys[m] |= (unsigned long long)((uint32_t)(a + 32768) & 0xFFFFu) << (16 * k);
         }
         __syncwarp();
     }

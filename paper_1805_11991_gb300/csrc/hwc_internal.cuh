@@ -59,9 +59,9 @@ struct Tables {
     // Fan-out rows (q <= 63): bit c of row l is 1 iff chi(alpha^l + c) = -1 for
     // the F_q digit c; the top bit (31 or 63) marks rows with alpha^l in F_q^x,
     // where alpha^l + c = 0 for the digit c = zdig[l / (L/(q-1))].
-    uint32_t *d_rows32 = nullptr;   // [L] when q <= 31
-    unsigned long long *d_rows64 = nullptr;   // [L] when q <= 63
-    uint8_t *d_zdig = nullptr;      // [q-1]
+    uint32_t *d_rows32 = nullptr;   // [L + 1] when q <= 31; row L is y = 0
+    unsigned long long *d_rows64 = nullptr;   // [L + 1] when q <= 63
+    uint8_t *d_zdig = nullptr;      // [q]
     // F_q arithmetic on digits (k = 1, q <= 63): a*b, a-b (u8 [q*q]), 1/a (u8 [q])
     uint8_t *d_fq_mul = nullptr;
     uint8_t *d_fq_sub = nullptr;
@@ -96,6 +96,7 @@ struct KJob {
     uint32_t barrett[kMaxG];          // floor(2^32 / L)
     uint32_t tab_off[kMaxG];          // u16 offset of the table in smem (smem kinds)
     uint32_t tab_kind[kMaxG];         // TabKind
+    uint32_t tab_pad[kMaxG];          // 1: smem table padded by one u32 word per 32 (TabP)
     uint32_t coef_off[kMaxG];         // u32 offset of coef_log in smem (after tables)
     const uint16_t *zech3[kMaxG];
     const uint16_t *zech2[kMaxG];
@@ -174,13 +175,29 @@ const void *fan2_kernel(int D);
 const void *fan2_kernel_a(int D);   // fan2_a.cu, D = 3..6
 const void *fan2_kernel_b(int D);   // fan2_b.cu, D = 7..10
 constexpr int kFan2WarpsHost = 4;   // warps per CTA of the two-level kernel
-// per-warp shared scratch bytes of the two-level kernel for q:
-// U[64] | acc[q^2] | n0[q] | square-free bits[ceil(q^2/32)]
-inline uint32_t fan2_warp_bytes(uint32_t q)
+// Per-warp shared scratch of the two-level kernel for q (S = floor(32/q)
+// lanes per value of c_1; offsets in bytes):
+//   U[us] u32: staged log u(x) for 64 points; us = 96 when 64/S is not a
+//              multiple of 8 (the lanes' 8-point blocks overrun 64), else 64
+//   acc[S q][q] u16: per-lane (c_1, s) rows of 2 cnt + z for every c_0
+//   rq[16][32] u16: per-lane queue of row indices with a zero digit
+//   sqf[ceil(q^2/32)] u32: square-free member bits
+constexpr uint32_t kFan2Queue = 16;
+struct Fan2Layout {
+    uint32_t us, acc_off, rq_off, sqf_off, bytes;
+};
+__host__ __device__ inline Fan2Layout fan2_layout(uint32_t q)
 {
-    const uint32_t qq = q * q, nw = (qq + 31) / 32;
-    return (4u * (64 + qq + q + nw) + 15u) & ~15u;
+    Fan2Layout l;
+    const uint32_t S = 32 / q, qq = q * q, nw = (qq + 31) / 32;
+    l.us = (S == 1 || S == 2 || S == 4 || S == 8) ? 64 : 96;
+    l.acc_off = 4 * l.us;
+    l.rq_off = l.acc_off + ((2 * S * qq + 3) & ~3u);
+    l.sqf_off = l.rq_off + 2 * kFan2Queue * 32;
+    l.bytes = (l.sqf_off + 4 * nw + 15) & ~15u;
+    return l;
 }
+inline uint32_t fan2_warp_bytes(uint32_t q) { return fan2_layout(q).bytes; }
 // launch shape of the two-level kernel for jobs with these smem needs: the
 // block (4, 8 or 16 warps) that keeps most warps resident; *smem receives the
 // dynamic shared memory of that block

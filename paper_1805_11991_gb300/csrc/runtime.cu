@@ -101,15 +101,23 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit)
     uint32_t kind[kMaxG];
     for (uint32_t k = 0; k < j.g; ++k)
         kind[k] = j.zech3[k] ? kTabTripleSmem : (j.zech2[k] ? kTabDoubleSmem : kTabDoubleGlobal);
+    // the two-level kernel's lanes b read Zech entries log b apart: multiples
+    // of s = L/(q-1).  For s = 0 mod 4 those fall on few banks unless the
+    // table carries one pad word per 32.
+    uint32_t pad[kMaxG];
+    for (uint32_t k = 0; k < j.g; ++k) pad[k] = (j.method == 2 && (j.L[k] / (j.q - 1)) % 4 == 0) ? 1u : 0u;
     auto words = [&](uint32_t k) -> uint64_t {
-        if (kind[k] == kTabTripleSmem) return ((3ull * j.L[k] + 1 + 7) / 8) * 8;
-        if (kind[k] == kTabDoubleSmem) return ((2ull * j.L[k] + 1 + 7) / 8) * 8;
-        return 0;
+        uint64_t n = 0;
+        if (kind[k] == kTabTripleSmem) n = 3ull * j.L[k] + 1;
+        else if (kind[k] == kTabDoubleSmem) n = 2ull * j.L[k] + 1;
+        else return 0;
+        if (pad[k]) n += 2 * ((n + 63) / 64);
+        return ((n + 7) / 8) * 8;
     };
     auto fan_bytes = [&](void) -> uint64_t {
         if (j.method == 0) return 0;
         uint64_t b = 0;
-        for (uint32_t k = 0; k < j.g; ++k) b += 4ull * j.words * j.L[k] + ((j.q + 15) / 16) * 16;
+        for (uint32_t k = 0; k < j.g; ++k) b += ((4ull * j.words * (j.L[k] + 1) + 15) / 16) * 16 + ((j.q + 15) / 16) * 16;
         b += ((2ull * j.q * j.q + j.q + 15) / 16) * 16;
         if (j.method == 2) b += 16 + (uint64_t)kFan2WarpsHost * fan2_warp_bytes(j.q);   // smallest block
         return b;
@@ -145,6 +153,7 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit)
     uint32_t off = 0;
     for (uint32_t k = 0; k < kMaxG; ++k) {
         j.tab_kind[k] = k < j.g ? kind[k] : kTabDoubleGlobal;
+        j.tab_pad[k] = (k < j.g && kind[k] != kTabDoubleGlobal) ? pad[k] : 0u;
         j.tab_off[k] = off;
         if (k < j.g) off += (uint32_t)words(k);
     }
@@ -159,7 +168,7 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit)
         j.row_off[k] = bytes;
         j.zdig_off[k] = bytes;
         if (j.method != 0 && k < j.g) {
-            bytes += 4 * j.words * j.L[k];
+            bytes += 4 * j.words * (j.L[k] + 1);
             bytes = (bytes + 15) / 16 * 16;
             j.zdig_off[k] = bytes;
             bytes += ((j.q + 15) / 16) * 16;

@@ -286,7 +286,15 @@ __global__ void k_rows(uint32_t q, uint32_t L, const uint32_t *__restrict__ zech
                        const uint32_t *__restrict__ coef_log, uint32_t *rows32,
                        unsigned long long *rows64)
 {
-    for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < L; l += gridDim.x * blockDim.x) {
+    for (uint32_t l = blockIdx.x * blockDim.x + threadIdx.x; l <= L; l += gridDim.x * blockDim.x) {
+        if (l == L) {   // y = 0: bit c says chi(e_c) = -1; y + e_0 = 0
+            unsigned long long m = 0;
+            for (uint32_t c = 1; c < q; ++c)
+                if (coef_log[c] & 1u) m |= 1ull << c;
+            if (rows32) rows32[L] = (uint32_t)m | 0x80000000u;
+            if (rows64) rows64[L] = m | (1ull << 63);
+            continue;
+        }
         unsigned long long m = l & 1u;   // c = 0: chi(alpha^l) = (-1)^l
         bool zero = false;
         for (uint32_t c = 1; c < q; ++c) {
@@ -301,10 +309,12 @@ __global__ void k_rows(uint32_t q, uint32_t L, const uint32_t *__restrict__ zech
     }
 }
 
-// zdig[m]: the digit c with alpha^(m s) + e_c = 0, s = L/(q-1)
+// zdig[m]: the digit c with alpha^(m s) + e_c = 0, s = L/(q-1); zdig[q-1] = 0
+// stands for y = 0 (row index L), where y + e_0 = 0
 __global__ void k_zdig(uint32_t q, uint32_t L, const uint32_t *__restrict__ coef_log, uint8_t *zdig)
 {
     const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c == 0) zdig[q - 1] = 0;
     if (c == 0 || c >= q) return;
     const uint32_t s = L / (q - 1);
     const uint32_t l = (coef_log[c] + L / 2) % L;   // log(-e_c)
@@ -521,13 +531,13 @@ int tables_build(uint32_t q, uint32_t k, Tables **out)
     // 4. fan-out rows (digits fit a 64-bit row)
     if (q <= 63) {
         bool rok = cudaMalloc(&t->d_zdig, q) == cudaSuccess;
-        if (rok && q <= 31) rok = cudaMalloc(&t->d_rows32, sizeof(uint32_t) * L) == cudaSuccess;
-        if (rok) rok = cudaMalloc(&t->d_rows64, sizeof(unsigned long long) * L) == cudaSuccess;
+        if (rok && q <= 31) rok = cudaMalloc(&t->d_rows32, sizeof(uint32_t) * (L + 1)) == cudaSuccess;
+        if (rok) rok = cudaMalloc(&t->d_rows64, sizeof(unsigned long long) * (L + 1)) == cudaSuccess;
         if (!rok) {
             cudaFree(d_best);
             return fail(set_error(HWC_ERR_NOMEM, "cudaMalloc of fan-out rows for Q=%u failed", t->Q));
         }
-        k_rows<<<std::max(1u, std::min(4096u, (L + 255) / 256)), 256>>>(q, L, t->d_zech, t->d_coef_log,
+        k_rows<<<std::max(1u, std::min(4096u, (L + 256) / 256)), 256>>>(q, L, t->d_zech, t->d_coef_log,
                                                                          t->d_rows32, t->d_rows64);
         k_zdig<<<1, 64>>>(q, L, t->d_coef_log, t->d_zdig);
         if (k == 1) {

@@ -84,8 +84,14 @@ def config2_q31d5():
     return [JobSpec(2, 31, MONIC_NOSUB, 5)]
 
 
+def config2_q31d6():
+    """The largest job of config 2 (q=31, degree 6, 31^5 members, 29,791 groups
+    of q^2 members): the small case used for profiles of the two-level kernel."""
+    return [JobSpec(2, 31, MONIC_NOSUB, 6)]
+
+
 CONFIGS = {"config1": config1, "config2": config2, "config3": config3, "config4": config4,
-           "config5": config5, "config2_q31d5": config2_q31d5}
+           "config5": config5, "config2_q31d5": config2_q31d5, "config2_q31d6": config2_q31d6}
 
 
 def poisson_arrivals(n: int, rate_per_s: float, seed: int = 11) -> np.ndarray:
