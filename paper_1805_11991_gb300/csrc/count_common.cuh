@@ -14,9 +14,10 @@ struct TabS {   // u16 table in shared memory
     __device__ __forceinline__ uint32_t operator[](uint32_t u) const { return t[u]; }
 };
 template <bool PAD>
-struct TabP {   // u16 table in shared memory; PAD: entry i at i + 2 floor(i / 64)
+struct TabP {   // staged two-level Zech table: index u at u + 64; PAD: entry i at i + 2 floor(i / 64)
     const uint16_t *t;
-    __device__ __forceinline__ uint32_t operator[](uint32_t u) const { return PAD ? t[u + ((u >> 6) << 1)] : t[u]; }
+    __device__ __forceinline__ uint32_t at(uint32_t i) const { return PAD ? t[i + ((i >> 6) << 1)] : t[i]; }
+    __device__ __forceinline__ uint32_t operator[](uint32_t u) const { return at(u + kFan2Prefix); }
 };
 struct TabG {   // u32 table in global memory (L1/L2 resident)
     const uint32_t *t;
@@ -221,19 +222,32 @@ __device__ void stage_job(const KJob &J, uint8_t *smem)
             const uint32_t n = (tri ? 3 : 2) * J.L[k] + 1;
             const uint16_t *src = tri ? J.zech3[k] : J.zech2[k];
             uint16_t *dst = s16 + J.tab_off[k];
-            if (J.tab_pad[k])   // entry i at i + 2 floor(i / 64)
-                for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) dst[i + ((i >> 6) << 1)] = src[i];
-            else
+            if (J.method == 2) {   // periodic prefix, poison 0xFFFF, optional pad word per 32
+                const int Li = (int)J.L[k];
+                for (uint32_t i = threadIdx.x; i < n + kFan2Prefix; i += blockDim.x) {
+                    const int u = (int)i - (int)kFan2Prefix;
+                    uint32_t v = src[u >= 0 ? u : ((u % Li) + Li) % Li];
+                    if (v >= J.L[k]) v = 0xFFFFu;
+                    dst[J.tab_pad[k] ? i + ((i >> 6) << 1) : i] = (uint16_t)v;
+                }
+            } else {
                 for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+            }
         }
         const uint32_t *src = J.coef_log[k];
         uint32_t *dst = s32 + J.coef_off[k];
         for (uint32_t i = threadIdx.x; i < J.q; i += blockDim.x) dst[i] = src[i];
         if (J.method != 0) {
-            const uint32_t nw = (J.L[k] + 1) * J.words;   // row L: y = 0
+            const uint32_t L = J.L[k];
             const uint32_t *rs = reinterpret_cast<const uint32_t *>(J.rows[k]);
             uint32_t *rd = reinterpret_cast<uint32_t *>(smem + J.row_off[k]);
-            for (uint32_t i = threadIdx.x; i < nw; i += blockDim.x) rd[i] = rs[i];
+            if (J.method == 2) {   // rows[i mod L] for i < L + 8, then y = 0 (row L of the table)
+                for (uint32_t i = threadIdx.x; i <= L + kFan2ZeroRow; i += blockDim.x)
+                    rd[i] = rs[i < L ? i : (i < L + kFan2ZeroRow ? (i - L) % L : L)];
+            } else {
+                const uint32_t nw = (L + 1) * J.words;   // row L: y = 0
+                for (uint32_t i = threadIdx.x; i < nw; i += blockDim.x) rd[i] = rs[i];
+            }
             uint8_t *zd = smem + J.zdig_off[k];
             for (uint32_t i = threadIdx.x; i < J.q; i += blockDim.x) zd[i] = J.zdig[k][i];
         }

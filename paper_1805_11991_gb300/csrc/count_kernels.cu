@@ -143,6 +143,12 @@ int max_ctas_per_sm(int D, uint32_t method, uint32_t words, int block, uint32_t 
     int n = 0;
     KernelFn fn = kernel_for(D, method, words, true);
     if (!fn) return set_error(HWC_ERR_ARG, "degree %d has no kernel", D);
+    cudaFuncAttributes fa{};
+    HWC_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
+    if (block > fa.maxThreadsPerBlock) {   // above the kernel's launch bound
+        *out = 0;
+        return HWC_OK;
+    }
     HWC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, smem_bytes));
     *out = n;
     return HWC_OK;

@@ -63,50 +63,59 @@ __device__ __forceinline__ void flush_planes(uint32_t (&P)[kFan2Planes], uint16_
     for (int b = 0; b < kFan2Planes; ++b) P[b] = 0;
 }
 
-// the lane's queued points with y in F_q (y + c = 0 for one digit c): z(b, c) += 1
+// the lane's queued points with y in F_q (y + c = 0 for one digit c): z(b, c) += 1.
+// Entries are staged row indices: i < L + 8 stands for log y = i mod L,
+// L + 8 for y = 0 (digit 0).
 __device__ __forceinline__ void drain_queue(const uint16_t *rq, uint32_t qn, int lane, const uint8_t *zdig,
-                                            uint32_t zdiv, uint16_t *acc_row)
+                                            uint32_t zdiv, uint32_t L, uint16_t *acc_row)
 {
     for (uint32_t i = 0; i < qn; ++i) {
-        const uint32_t l = rq[i * 32 + lane];
-        const uint32_t d = zdig[zdiv ? __umulhi(l, zdiv) : l];
+        uint32_t l = rq[i * 32 + lane];
+        uint32_t d = 0;
+        if (l != L + kFan2ZeroRow) {
+            if (l >= L) l %= L;
+            d = zdig[zdiv ? __umulhi(l, zdiv) : l];
+        }
         acc_row[d] = (uint16_t)(acc_row[d] + 1);
     }
 }
 
-// One block of 8 consecutive points x = alpha^(j0 + i), i = i0 + t0 .. + 7,
-// for lane (b, s).  Phases over the 8 points so that their lookups overlap:
-// staged log u -> Zech addition y_b = u + b x (eq. 2.1) -> fan-out row of
-// y_b.  The row of y_b carries bit c = [chi(y_b + c) = -1] and a flag for
-// y_b in F_q (y_b = 0 included: row L), whose zero digit goes to the queue.
-// GEN: some points of the block may be missing (okm) or have u = 0.
+// One block of 8 consecutive points x = alpha^(j0 + i) for lane (b, s), with
+// lb = log(b x) of the first point reduced mod L (later points lb + v, not
+// reduced).  Phases over the 8 points so that their lookups overlap: staged
+// log u -> Zech addition y_b = u + b x = b x (1 + u / (b x)) (eq. 2.1) ->
+// fan-out row of y_b.  Row bit c is [chi(y_b + c) = -1]; the top bit flags
+// y_b in F_q (y_b = 0 included), whose zero digit goes to the lane's queue.
+// The row's top bit is counted too, in a position no member reads.
+// GEN: points outside okm are dropped, and u may be 0.
 template <bool GEN, class Tab>
 __device__ __forceinline__ void fan2_block(const Tab T, const uint32_t *__restrict__ rows, const uint32_t *Us,
-                                           uint32_t L, uint32_t &lbx, bool b0, bool role, uint32_t okm,
-                                           uint16_t *rq, int lane, uint32_t &qn, uint32_t (&a)[8])
+                                           uint32_t L, uint32_t lb, bool b0, uint32_t okm, uint16_t *rq, int lane,
+                                           uint32_t &qn, uint32_t (&a)[8])
 {
     const uint4 w0 = *reinterpret_cast<const uint4 *>(Us);
     const uint4 w1 = *reinterpret_cast<const uint4 *>(Us + 4);
     const uint32_t U[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+    // staged Zech index of log u - log(b x) + L: in [58, 2L + 64]
+    const uint32_t C = L + kFan2Prefix - lb;
     uint32_t ly[8];
 #pragma unroll
     for (int v = 0; v < 8; ++v) {
-        // log(u + b x) = log(b x) + Z(log u - log(b x)); index in [1, 2L] for u != 0
-        const uint32_t z = T[U[v] + (L - lbx)];
-        uint32_t t = lbx + z;            // < 2L, or >= 2L when u + b x = 0 (z poisoned)
-        t = min(t, t - L);               // mod L; the poisoned case stays >= L
-        t = min(t, L);                   // row L: y = 0
-        if (GEN) t = (U[v] >= L) ? lbx : t;   // u = 0: y = b x
-        ly[v] = b0 ? U[v] : t;           // b = 0: y = u
-        lbx = (lbx + 1 == L) ? 0u : lbx + 1;
+        const uint32_t z = T.at(U[v] + C - v);
+        uint32_t t = lb + v + z;          // < 2L + 6, or >= 65535 when u + b x = 0
+        t = min(t, t - L);                // congruent mod L, < L + 6; poisoned: >= L + 8
+        t = min(t, L + kFan2ZeroRow);     // row L + 8: y = 0
+        if (GEN) t = (U[v] >= L) ? lb + v : t;   // u = 0: y = b x
+        if (GEN) ly[v] = b0 ? (U[v] >= L ? L + kFan2ZeroRow : U[v]) : t;
+        else ly[v] = b0 ? U[v] : t;       // b = 0: y = u
     }
 #pragma unroll
     for (int v = 0; v < 8; ++v) {
         const uint32_t r = rows[ly[v]];
-        const bool ok = GEN ? ((okm >> v) & 1u) != 0 : role;
-        a[v] = (!GEN || ok) ? (r & 0x7FFFFFFFu) : 0u;
+        const bool ok = !GEN || ((okm >> v) & 1u);
+        a[v] = ok ? r : 0u;
         rq[qn * 32 + lane] = (uint16_t)ly[v];   // kept when the flag is set
-        qn += (ok && (r >> 31)) ? 1u : 0u;
+        qn += (ok && (int)r < 0) ? 1u : 0u;
     }
 }
 
@@ -120,7 +129,7 @@ __device__ __forceinline__ void group2_field(const KJob &J, int k, const uint8_t
     const TabP<PAD> T{reinterpret_cast<const uint16_t *>(smem) + J.tab_off[k]};
     const uint32_t L = J.L[k];
     const uint32_t bar = J.barrett[k];
-    const uint32_t *rows = reinterpret_cast<const uint32_t *>(smem + J.row_off[k]);   // [L + 1]
+    const uint32_t *rows = reinterpret_cast<const uint32_t *>(smem + J.row_off[k]);   // [L + 9]
     const uint8_t *zdig = smem + J.zdig_off[k];
     const uint32_t zdiv = J.zdiv[k];
     const uint32_t *coefk = reinterpret_cast<const uint32_t *>(smem) + J.coef_off[k];
@@ -143,17 +152,18 @@ __device__ __forceinline__ void group2_field(const KJob &J, int k, const uint8_t
         const uint32_t nb = min(64u, L - j0);   // points in this batch
         if (pow2S && nb == 64 && !uzero) {
             const uint32_t per = 64 / S, i0 = s * per;
-            uint32_t lbx = addmod(lam_b, j0 + i0, L);
+            uint32_t lb = addmod(lam_b, j0 + i0, L);
             for (uint32_t t0 = 0; t0 < per; t0 += 8) {
                 uint32_t a[8];
-                fan2_block<false>(T, rows, Us + i0 + t0, L, lbx, b0, role, 0u, rq, lane, qn, a);
+                fan2_block<false>(T, rows, Us + i0 + t0, L, lb, b0, 0u, rq, lane, qn, a);
+                lb = addmod(lb, 8u % L, L);
                 add8_p10(P, a);
                 if (++nblk == kFan2FlushBlocks) {
-                    flush_planes(P, acc_row, J.q, role);
+                    flush_planes(P, acc_row, J.q, true);
                     nblk = 0;
                 }
                 if (__any_sync(0xFFFFFFFFu, qn > kFan2Queue - 8)) {
-                    drain_queue(rq, qn, lane, zdig, zdiv, acc_row);
+                    drain_queue(rq, qn, lane, zdig, zdiv, L, acc_row);
                     qn = 0;
                 }
             }
@@ -161,27 +171,28 @@ __device__ __forceinline__ void group2_field(const KJob &J, int k, const uint8_t
             // lane chunks of a multiple of 8 points; reads past 64 hit the
             // zeroed slack of U and are masked
             const uint32_t per = (((nb + S - 1) / S) + 7) & ~7u, i0 = s * per;
-            uint32_t lbx = addmod(lam_b, (j0 + i0) % L, L);
+            uint32_t lb = addmod(lam_b, (j0 + i0) % L, L);
             for (uint32_t t0 = 0; t0 < per; t0 += 8) {
                 const int nv = role ? min(8, max(0, (int)nb - (int)(i0 + t0))) : 0;
                 const uint32_t okm = (1u << nv) - 1u;
                 uint32_t a[8];
-                fan2_block<true>(T, rows, Us + i0 + t0, L, lbx, b0, role, okm, rq, lane, qn, a);
+                fan2_block<true>(T, rows, Us + i0 + t0, L, lb, b0, okm, rq, lane, qn, a);
+                lb = addmod(lb, 8u % L, L);
                 add8_p10(P, a);
                 if (++nblk == kFan2FlushBlocks) {
-                    flush_planes(P, acc_row, J.q, role);
+                    flush_planes(P, acc_row, J.q, true);
                     nblk = 0;
                 }
                 if (__any_sync(0xFFFFFFFFu, qn > kFan2Queue - 8)) {
-                    drain_queue(rq, qn, lane, zdig, zdiv, acc_row);
+                    drain_queue(rq, qn, lane, zdig, zdiv, L, acc_row);
                     qn = 0;
                 }
             }
         }
         __syncwarp();   // U is rewritten by the next batch
     }
-    flush_planes(P, acc_row, J.q, role);
-    drain_queue(rq, qn, lane, zdig, zdiv, acc_row);
+    flush_planes(P, acc_row, J.q, true);
+    drain_queue(rq, qn, lane, zdig, zdiv, L, acc_row);
 }
 
 // Square-freeness of the q members f_c = g_b + c (c in F_q) that share
@@ -362,8 +373,8 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
     const bool role = (uint32_t)lane < S * q;
     const uint32_t b = role ? (uint32_t)lane % q : 0;
     const uint32_t s = role ? (uint32_t)lane / q : 0;
-    uint16_t *acc_row = acc + (role ? (uint32_t)lane * q : 0u);
-    const uint32_t acc_words = (S * qq + 1) / 2;
+    uint16_t *acc_row = acc + (uint32_t)lane * q;   // lanes past S q: rows no member reads
+    const uint32_t acc_words = 16 * q;
 
 #pragma unroll 1
     for (int k = 0; k < G; ++k) {
@@ -428,8 +439,10 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
     __syncwarp();
 }
 
+// threads per CTA at most: 24 warps at <= 80 registers for degrees <= 6, 16
+// warps above (whose longer coefficient arrays would spill at 80)
 template <int D>
-__global__ void __launch_bounds__(512, 1)
+__global__ void __launch_bounds__(D <= 6 ? 768 : 512, 1)
     k_fan2_persistent(const KJob *__restrict__ jobs, const uint64_t *__restrict__ item_start, uint32_t n_jobs,
                       uint64_t n_items, unsigned long long *counter, uint32_t item_tiles)
 {

@@ -179,27 +179,34 @@ constexpr int kFan2WarpsHost = 4;   // warps per CTA of the two-level kernel
 // lanes per value of c_1; offsets in bytes):
 //   U[us] u32: staged log u(x) for 64 points; us = 96 when 64/S is not a
 //              multiple of 8 (the lanes' 8-point blocks overrun 64), else 64
-//   acc[S q][q] u16: per-lane (c_1, s) rows of 2 cnt + z for every c_0
+//   acc[32][q] u16: per-lane rows of 2 cnt + z for every c_0 (lane s q + b
+//              holds (c_1 = b, chunk s); lanes past S q fill unused rows)
 //   rq[16][32] u16: per-lane queue of row indices with a zero digit
 //   sqf[ceil(q^2/32)] u32: square-free member bits
 constexpr uint32_t kFan2Queue = 16;
+// The two-level kernel stages each Zech table behind a prefix of 64 entries
+// (the table continued periodically to negative indices) with the poison
+// value 0xFFFF, and each fan-out row table as rows[i mod L] for i < L + 8
+// followed by the row of y = 0 at L + 8.
+constexpr uint32_t kFan2Prefix = 64;
+constexpr uint32_t kFan2ZeroRow = 8;   // row index L + 8
 struct Fan2Layout {
     uint32_t us, acc_off, rq_off, sqf_off, bytes;
 };
 __host__ __device__ inline Fan2Layout fan2_layout(uint32_t q)
 {
     Fan2Layout l;
-    const uint32_t S = 32 / q, qq = q * q, nw = (qq + 31) / 32;
+    const uint32_t S = 32 / q, nw = (q * q + 31) / 32;
     l.us = (S == 1 || S == 2 || S == 4 || S == 8) ? 64 : 96;
     l.acc_off = 4 * l.us;
-    l.rq_off = l.acc_off + ((2 * S * qq + 3) & ~3u);
+    l.rq_off = l.acc_off + ((64 * q + 3) & ~3u);
     l.sqf_off = l.rq_off + 2 * kFan2Queue * 32;
     l.bytes = (l.sqf_off + 4 * nw + 15) & ~15u;
     return l;
 }
 inline uint32_t fan2_warp_bytes(uint32_t q) { return fan2_layout(q).bytes; }
 // launch shape of the two-level kernel for jobs with these smem needs: the
-// block (4, 8 or 16 warps) that keeps most warps resident; *smem receives the
+// block (4, 8, 16 or 24 warps) that keeps most warps resident; *smem receives the
 // dynamic shared memory of that block
 struct Fan2Need {
     uint32_t warp_off, warp_bytes;

@@ -111,13 +111,17 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit)
         if (kind[k] == kTabTripleSmem) n = 3ull * j.L[k] + 1;
         else if (kind[k] == kTabDoubleSmem) n = 2ull * j.L[k] + 1;
         else return 0;
+        if (j.method == 2) n += kFan2Prefix;
         if (pad[k]) n += 2 * ((n + 63) / 64);
         return ((n + 7) / 8) * 8;
+    };
+    auto row_bytes = [&](uint32_t k) -> uint64_t {
+        return j.method == 2 ? 4ull * (j.L[k] + kFan2ZeroRow + 1) : 4ull * j.words * (j.L[k] + 1);
     };
     auto fan_bytes = [&](void) -> uint64_t {
         if (j.method == 0) return 0;
         uint64_t b = 0;
-        for (uint32_t k = 0; k < j.g; ++k) b += ((4ull * j.words * (j.L[k] + 1) + 15) / 16) * 16 + ((j.q + 15) / 16) * 16;
+        for (uint32_t k = 0; k < j.g; ++k) b += ((row_bytes(k) + 15) / 16) * 16 + ((j.q + 15) / 16) * 16;
         b += ((2ull * j.q * j.q + j.q + 15) / 16) * 16;
         if (j.method == 2) b += 16 + (uint64_t)kFan2WarpsHost * fan2_warp_bytes(j.q);   // smallest block
         return b;
@@ -168,7 +172,7 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit)
         j.row_off[k] = bytes;
         j.zdig_off[k] = bytes;
         if (j.method != 0 && k < j.g) {
-            bytes += 4 * j.words * (j.L[k] + 1);
+            bytes += (uint32_t)row_bytes(k);
             bytes = (bytes + 15) / 16 * 16;
             j.zdig_off[k] = bytes;
             bytes += ((j.q + 15) / 16) * 16;
@@ -460,7 +464,7 @@ int hwc::choose_shape_fan2(int D, const Fan2Need *needs, size_t n, LaunchShape *
     const int sms = device_sm_count();
     const uint32_t limit = device_smem_optin() - 4096;
     int best_warps = -1;
-    for (int block : {512, 256, 128}) {
+    for (int block : {768, 512, 256, 128}) {
         const uint32_t W = (uint32_t)block / 32;
         uint32_t need = 0;
         for (size_t i = 0; i < n; ++i) need = std::max(need, needs[i].warp_off + W * needs[i].warp_bytes);
