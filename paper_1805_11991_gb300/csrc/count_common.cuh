@@ -252,6 +252,10 @@ __device__ void stage_job(const KJob &J, uint8_t *smem)
             for (uint32_t i = threadIdx.x; i < J.q; i += blockDim.x) zd[i] = J.zdig[k][i];
         }
     }
+    if (J.dense_off) {   // the CTA's dense (a_1, a_2) counters start at zero
+        uint32_t *dn = reinterpret_cast<uint32_t *>(smem + J.dense_off);
+        for (uint32_t i = threadIdx.x; i < J.dense_n; i += blockDim.x) dn[i] = 0;
+    }
     if (J.method != 0) {   // F_q digit arithmetic: mul | sub | inv
         const uint32_t qq = J.q * J.q;
         uint8_t *d = smem + J.fq_off;

@@ -426,6 +426,23 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
     }
     if (J.member_counts) return;
     __syncwarp();
+    if (J.dense_off) {   // g <= 2: the CTA's shared (a_1, a_2) counters
+        uint32_t *dense = reinterpret_cast<uint32_t *>(const_cast<uint8_t *>(smem) + J.dense_off);
+        for (uint32_t t = 0; t < nw; ++t) {
+            const uint32_t m = t * 32 + lane;
+            if (m < qq && ((sqfw[t] >> lane) & 1u)) {
+                const unsigned long long key = keys[m];
+                const int i1 = (int)(key & 0xFFFFu) - 32768 + J.dense_b1;
+                const int i2 = G == 2 ? (int)((key >> 16) & 0xFFFFu) - 32768 + J.dense_b2 : 0;
+                if (i1 >= 0 && i1 <= 2 * J.dense_b1 && i2 >= 0 && i2 <= 2 * J.dense_b2)
+                    atomicAdd(&dense[(uint32_t)i1 * J.dense_w2 + (uint32_t)i2], 1u);
+                else
+                    hist_insert(J, key, 1u);   // outside the Hasse-Weil box: not for a smooth curve
+            }
+        }
+        __syncwarp();
+        return;
+    }
     for (uint32_t t = 0; t < nw; ++t) {
         const uint32_t m = t * 32 + lane;
         const bool sq = m < qq && ((sqfw[t] >> lane) & 1u);
@@ -437,6 +454,22 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
         }
     }
     __syncwarp();
+}
+
+// the CTA's dense (a_1, a_2) counters into the job's histogram (all threads;
+// the counters must be complete: call after a barrier)
+__device__ void flush_dense(const KJob &J, const uint8_t *smem)
+{
+    const uint32_t *dense = reinterpret_cast<const uint32_t *>(smem + J.dense_off);
+    for (uint32_t i = threadIdx.x; i < J.dense_n; i += blockDim.x) {
+        const uint32_t c = dense[i];
+        if (!c) continue;
+        const int a1 = (int)(i / J.dense_w2) - J.dense_b1;
+        const int a2 = (int)(i % J.dense_w2) - J.dense_b2;
+        unsigned long long key = (unsigned long long)((uint32_t)(a1 + 32768) & 0xFFFFu);
+        if (J.g == 2) key |= (unsigned long long)((uint32_t)(a2 + 32768) & 0xFFFFu) << 16;
+        hist_insert(J, key, c);
+    }
 }
 
 // threads per CTA at most: 24 warps at <= 80 registers for degrees <= 6, 16
@@ -465,7 +498,11 @@ __global__ void __launch_bounds__(D <= 6 ? 768 : 512, 1)
         }
         const int jb = (int)lo;
         if (jb != cur) {
-            if (cur >= 0) flush_stats(jobs[cur], st, lane);
+            if (cur >= 0) {
+                flush_stats(jobs[cur], st, lane);
+                if (jobs[cur].dense_off) flush_dense(jobs[cur], smem);
+                __syncthreads();
+            }
             stage_job(jobs[jb], smem);
             __syncthreads();
             cur = jb;
@@ -477,7 +514,10 @@ __global__ void __launch_bounds__(D <= 6 ? 768 : 512, 1)
         for (uint64_t t = t0 + warp; t < t1; t += nwp) process_group2<D>(J, t, smem, wsm, lane, st);
         __syncthreads();
     }
-    if (cur >= 0) flush_stats(jobs[cur], st, lane);
+    if (cur >= 0) {
+        flush_stats(jobs[cur], st, lane);
+        if (jobs[cur].dense_off) flush_dense(jobs[cur], smem);
+    }
 }
 
 template <int D>

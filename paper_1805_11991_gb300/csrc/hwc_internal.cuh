@@ -115,6 +115,9 @@ struct KJob {
     uint32_t zdig_off[kMaxG];         // byte offset of zdig in smem
     uint32_t zdiv[kMaxG];             // ceil(2^32 / (L/(q-1))): l / s by a high multiply
     uint32_t warp_off, warp_bytes;    // per-warp scratch in smem (method 2)
+    uint32_t dense_off;               // method 2, g <= 2: smem offset of the CTA's (a_1, a_2) counters; 0: none
+    uint32_t dense_w2, dense_n;       //   counter (a_1 + B_1) * w2 + (a_2 + B_2), n counters
+    int32_t dense_b1, dense_b2;       //   Hasse-Weil bounds B_k = floor(2 g sqrt(q^k)) (B_2 = 0 for g = 1)
     unsigned long long *wkeys;        // per-warp member keys in global memory (method 2):
     uint32_t wkeys_stride, pad3;      //   slot blockIdx.x * warps + warp, stride q^2
     const uint8_t *fq_mul, *fq_sub, *fq_inv;   // digit arithmetic of F_q (fan-out jobs)

@@ -96,6 +96,14 @@ static int validate_job(const hwc_job_t &j, uint64_t *fam_n)
 // Starts from the fastest layout per field (tripled Zech table in smem) and
 // moves the largest tables to cheaper-in-space layouts until the job fits.
 // Returns false if a fan-out job cannot keep its rows in shared memory.
+static uint64_t isqrt_u64(uint64_t v)   // floor(sqrt(v))
+{
+    uint64_t x = (uint64_t)std::sqrt((double)v);
+    while (x * x > v) --x;
+    while ((x + 1) * (x + 1) <= v) ++x;
+    return x;
+}
+
 bool layout_job_smem(KJob &j, uint32_t smem_limit)
 {
     uint32_t kind[kMaxG];
@@ -182,8 +190,25 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit)
     if (j.method != 0) bytes += ((2 * j.q * j.q + j.q + 15) / 16) * 16;
     j.warp_off = 0;
     j.warp_bytes = 0;
+    j.dense_off = 0;
     if (j.method == 2) {
         bytes = (bytes + 15) / 16 * 16;
+        // g <= 2: the CTA counts (a_1, a_2) in a dense box of shared counters
+        // when that leaves room for 24 warps
+        if (j.g <= 2) {
+            const int32_t b1 = (int32_t)isqrt_u64(4ull * j.g * j.g * j.q);
+            const int32_t b2 = j.g == 2 ? (int32_t)(2 * j.g * j.q) : 0;
+            const uint32_t n = (uint32_t)(2 * b1 + 1) * (uint32_t)(2 * b2 + 1);
+            const uint32_t dbytes = (4 * n + 15) / 16 * 16;
+            if ((uint64_t)bytes + dbytes + 24ull * fan2_warp_bytes(j.q) + 16 <= smem_limit) {
+                j.dense_off = bytes;
+                j.dense_b1 = b1;
+                j.dense_b2 = b2;
+                j.dense_w2 = (uint32_t)(2 * b2 + 1);
+                j.dense_n = n;
+                bytes += dbytes;
+            }
+        }
         j.warp_off = bytes;
         j.warp_bytes = fan2_warp_bytes(j.q);
         bytes += kFan2WarpsHost * j.warp_bytes;
