@@ -65,12 +65,13 @@ __device__ __forceinline__ void flush_planes(uint32_t (&P)[kFan2Planes], uint16_
 
 // the lane's queued points with y in F_q (y + c = 0 for one digit c): z(b, c) += 1.
 // Entries are staged row indices: i < L + 8 stands for log y = i mod L,
-// L + 8 for y = 0 (digit 0).
+// L + 8 for y = 0 (digit 0).  The lane's entries sit at lane, lane + 32, ...;
+// qn = lane + 32 * (number of entries).
 __device__ __forceinline__ void drain_queue(const uint16_t *rq, uint32_t qn, int lane, const uint8_t *zdig,
                                             uint32_t zdiv, uint32_t L, uint16_t *acc_row)
 {
-    for (uint32_t i = 0; i < qn; ++i) {
-        uint32_t l = rq[i * 32 + lane];
+    for (uint32_t i = (uint32_t)lane; i < qn; i += 32) {
+        uint32_t l = rq[i];
         uint32_t d = 0;
         if (l != L + kFan2ZeroRow) {
             if (l >= L) l %= L;
@@ -90,7 +91,7 @@ __device__ __forceinline__ void drain_queue(const uint16_t *rq, uint32_t qn, int
 // GEN: points outside okm are dropped, and u may be 0.
 template <bool GEN, class Tab>
 __device__ __forceinline__ void fan2_block(const Tab T, const uint32_t *__restrict__ rows, const uint32_t *Us,
-                                           uint32_t L, uint32_t lb, bool b0, uint32_t okm, uint16_t *rq, int lane,
+                                           uint32_t L, uint32_t lb, bool b0, uint32_t okm, uint16_t *rq,
                                            uint32_t &qn, uint32_t (&a)[8])
 {
     const uint4 w0 = *reinterpret_cast<const uint4 *>(Us);
@@ -109,13 +110,16 @@ __device__ __forceinline__ void fan2_block(const Tab T, const uint32_t *__restri
         if (GEN) ly[v] = b0 ? (U[v] >= L ? L + kFan2ZeroRow : U[v]) : t;
         else ly[v] = b0 ? U[v] : t;       // b = 0: y = u
     }
+    // all 8 row loads before any queue store (a store may alias later loads)
+#pragma unroll
+    for (int v = 0; v < 8; ++v) a[v] = rows[ly[v]];
 #pragma unroll
     for (int v = 0; v < 8; ++v) {
-        const uint32_t r = rows[ly[v]];
-        const bool ok = !GEN || ((okm >> v) & 1u);
-        a[v] = ok ? r : 0u;
-        rq[qn * 32 + lane] = (uint16_t)ly[v];   // kept when the flag is set
-        qn += (ok && (int)r < 0) ? 1u : 0u;
+        if (GEN && !((okm >> v) & 1u)) a[v] = 0u;
+        if ((int)a[v] < 0) {   // flagged: y in F_q
+            rq[qn] = (uint16_t)ly[v];
+            qn += 32;
+        }
     }
 }
 
@@ -139,7 +143,7 @@ __device__ __forceinline__ void group2_field(const KJob &J, int k, const uint8_t
     uint32_t P[kFan2Planes];
 #pragma unroll
     for (int p = 0; p < kFan2Planes; ++p) P[p] = 0;
-    uint32_t nblk = 0, qn = 0;
+    uint32_t nblk = 0, qn = (uint32_t)lane;
     for (uint32_t j0 = 0; j0 < L; j0 += 64) {
         // log u(x) for the batch, two points per lane, staged for all lanes
         const uint32_t xA = j0 + lane, xB = j0 + 32 + lane;
@@ -155,16 +159,16 @@ __device__ __forceinline__ void group2_field(const KJob &J, int k, const uint8_t
             uint32_t lb = addmod(lam_b, j0 + i0, L);
             for (uint32_t t0 = 0; t0 < per; t0 += 8) {
                 uint32_t a[8];
-                fan2_block<false>(T, rows, Us + i0 + t0, L, lb, b0, 0u, rq, lane, qn, a);
+                fan2_block<false>(T, rows, Us + i0 + t0, L, lb, b0, 0u, rq, qn, a);
                 lb = addmod(lb, 8u % L, L);
                 add8_p10(P, a);
                 if (++nblk == kFan2FlushBlocks) {
                     flush_planes(P, acc_row, J.q, true);
                     nblk = 0;
                 }
-                if (__any_sync(0xFFFFFFFFu, qn > kFan2Queue - 8)) {
+                if (__any_sync(0xFFFFFFFFu, qn >= 32 * (kFan2Queue - 8 + 1))) {   // more than 8 entries
                     drain_queue(rq, qn, lane, zdig, zdiv, L, acc_row);
-                    qn = 0;
+                    qn = (uint32_t)lane;
                 }
             }
         } else {
@@ -176,16 +180,16 @@ __device__ __forceinline__ void group2_field(const KJob &J, int k, const uint8_t
                 const int nv = role ? min(8, max(0, (int)nb - (int)(i0 + t0))) : 0;
                 const uint32_t okm = (1u << nv) - 1u;
                 uint32_t a[8];
-                fan2_block<true>(T, rows, Us + i0 + t0, L, lb, b0, okm, rq, lane, qn, a);
+                fan2_block<true>(T, rows, Us + i0 + t0, L, lb, b0, okm, rq, qn, a);
                 lb = addmod(lb, 8u % L, L);
                 add8_p10(P, a);
                 if (++nblk == kFan2FlushBlocks) {
                     flush_planes(P, acc_row, J.q, true);
                     nblk = 0;
                 }
-                if (__any_sync(0xFFFFFFFFu, qn > kFan2Queue - 8)) {
+                if (__any_sync(0xFFFFFFFFu, qn >= 32 * (kFan2Queue - 8 + 1))) {   // more than 8 entries
                     drain_queue(rq, qn, lane, zdig, zdiv, L, acc_row);
-                    qn = 0;
+                    qn = (uint32_t)lane;
                 }
             }
         }
