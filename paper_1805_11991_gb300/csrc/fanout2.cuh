@@ -124,11 +124,12 @@ __device__ __forceinline__ void fan2_block(const Tab T, const uint32_t *__restri
 }
 
 // points of one field for the whole group (all q^2 members), lane role (b, s)
+// The chain constants (lam_i and the h chain) come from the warp's shared
+// parameters at every batch: the main loop keeps no registers for them.
 template <int D, bool TRIPLE, bool PAD>
-__device__ __forceinline__ void group2_field(const KJob &J, int k, const uint8_t *smem, const HChain<D> &H,
-                                             const uint32_t (&lam)[D + 1], uint32_t nz, uint32_t *Us,
-                                             uint16_t *acc_row, uint16_t *rq, int lane, bool role, uint32_t b,
-                                             uint32_t s, uint32_t S)
+__device__ __forceinline__ void group2_field(const KJob &J, int k, const uint8_t *smem, const HChain<D> *gH,
+                                             const uint32_t *glam, uint32_t nz, uint32_t *Us, uint16_t *acc_row,
+                                             uint16_t *rq, int lane, bool role, uint32_t b, uint32_t s, uint32_t S)
 {
     const TabP<PAD> T{reinterpret_cast<const uint16_t *>(smem) + J.tab_off[k]};
     const uint32_t L = J.L[k];
@@ -148,7 +149,13 @@ __device__ __forceinline__ void group2_field(const KJob &J, int k, const uint8_t
         // log u(x) for the batch, two points per lane, staged for all lanes
         const uint32_t xA = j0 + lane, xB = j0 + 32 + lane;
         uint32_t uA, uB;
-        log_y_pair<D, TRIPLE, TabP<PAD>, 2>(T, L, bar, H, lam, nz, xA < L ? xA : 0, xB < L ? xB : 0, uA, uB);
+        {
+            const HChain<D> H = *gH;
+            uint32_t lam[D + 1];
+#pragma unroll
+            for (int i = 0; i <= D; ++i) lam[i] = glam[i];
+            log_y_pair<D, TRIPLE, TabP<PAD>, 2>(T, L, bar, H, lam, nz, xA < L ? xA : 0, xB < L ? xB : 0, uA, uB);
+        }
         Us[lane] = uA;
         Us[32 + lane] = uB;
         const bool uzero = __any_sync(0xFFFFFFFFu, uA >= L || uB >= L);
@@ -315,6 +322,10 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
     uint16_t *acc = reinterpret_cast<uint16_t *>(wsm + lay.acc_off);
     uint16_t *rq = reinterpret_cast<uint16_t *>(wsm + lay.rq_off);
     uint32_t *sqfw = reinterpret_cast<uint32_t *>(wsm + lay.sqf_off);
+    uint32_t *gc = reinterpret_cast<uint32_t *>(wsm + lay.par_off);   // c_0..c_D
+    uint32_t *glam = gc + 12;                                          // lam_0..lam_D of the field
+    HChain<D> *gH = reinterpret_cast<HChain<D> *>(gc + 24);
+    static_assert(sizeof(HChain<D>) <= 4 * (64 - 24), "h chain exceeds the warp's parameter block");
     const uint32_t nw = (qq + 31) / 32;
     unsigned long long *keys =
         J.wkeys + ((uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * J.wkeys_stride;
@@ -328,9 +339,13 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
     // square-freeness: lane b settles the q members with c_1 = b at once
     for (uint32_t t = lane; t < nw; t += 32) sqfw[t] = 0;
     if (64 + (uint32_t)lane < lay.us) Us[64 + lane] = 0;   // slack read by 8-point blocks past 64
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i <= D; ++i) gc[i] = c[i];
+    }
     __syncwarp();
     if ((uint32_t)lane < q) {
-        const uint32_t mask = sqf_mask_for_b<D>(mulT, subT, invT, q, J.p, c, (uint32_t)lane);
+        const uint32_t mask = sqf_mask_for_b<D>(mulT, subT, invT, q, J.p, gc, (uint32_t)lane);
         // bits b*q .. b*q + q-1 of the member mask
         const uint32_t bit0 = (uint32_t)lane * q;
         const uint32_t w0 = bit0 >> 5, sh = bit0 & 31u;
@@ -384,25 +399,30 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
     for (int k = 0; k < G; ++k) {
         const uint32_t L = J.L[k], Q = J.Q[k];
         const uint32_t *coefk = s32 + J.coef_off[k];
-        uint32_t lam[D + 1];
+        if (lane == 0) {
+            uint32_t lam[D + 1];
 #pragma unroll
-        for (int i = 0; i <= D; ++i) lam[i] = coefk[c[i]];
-        HChain<D> H;
-        make_hchain<D, 2>(H, lam, nz, L);
+            for (int i = 0; i <= D; ++i) lam[i] = coefk[gc[i]];
+            HChain<D> H;
+            make_hchain<D, 2>(H, lam, nz, L);
+            *gH = H;
+#pragma unroll
+            for (int i = 0; i <= D; ++i) glam[i] = lam[i];
+        }
         for (uint32_t m = lane; m < acc_words; m += 32) reinterpret_cast<uint32_t *>(acc)[m] = 0;
         __syncwarp();
         const bool tri = J.tab_kind[k] == kTabTripleSmem;
         if (J.tab_pad[k]) {
-            if (tri) group2_field<D, true, true>(J, k, smem, H, lam, nz, Us, acc_row, rq, lane, role, b, s, S);
-            else group2_field<D, false, true>(J, k, smem, H, lam, nz, Us, acc_row, rq, lane, role, b, s, S);
+            if (tri) group2_field<D, true, true>(J, k, smem, gH, glam, nz, Us, acc_row, rq, lane, role, b, s, S);
+            else group2_field<D, false, true>(J, k, smem, gH, glam, nz, Us, acc_row, rq, lane, role, b, s, S);
         } else {
-            if (tri) group2_field<D, true, false>(J, k, smem, H, lam, nz, Us, acc_row, rq, lane, role, b, s, S);
-            else group2_field<D, false, false>(J, k, smem, H, lam, nz, Us, acc_row, rq, lane, role, b, s, S);
+            if (tri) group2_field<D, true, false>(J, k, smem, gH, glam, nz, Us, acc_row, rq, lane, role, b, s, S);
+            else group2_field<D, false, false>(J, k, smem, gH, glam, nz, Us, acc_row, rq, lane, role, b, s, S);
         }
         __syncwarp();
         // sum_x chi(f_{b,c}(x)) = (L - sum_s acc[s q + b][c]) + chi(c)   (x = 0: y = 0)
         int inf = 1;
-        if (D == 2 * G + 2) inf += (lam[D] & 1u) ? -1 : 1;
+        if (D == 2 * G + 2) inf += (glam[D] & 1u) ? -1 : 1;
         if ((uint32_t)lane < q) {
             const uint32_t cc = (uint32_t)lane;
             const uint32_t lc = coefk[cc];

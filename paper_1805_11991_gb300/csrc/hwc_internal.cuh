@@ -186,6 +186,7 @@ constexpr int kFan2WarpsHost = 4;   // warps per CTA of the two-level kernel
 //              holds (c_1 = b, chunk s); lanes past S q fill unused rows)
 //   rq[16][32] u16: per-lane queue of row indices with a zero digit
 //   sqf[ceil(q^2/32)] u32: square-free member bits
+//   par[64] u32: the group's digits c_i, the field's logs lam_i and h chain
 constexpr uint32_t kFan2Queue = 16;
 // The two-level kernel stages each Zech table behind a prefix of 64 entries
 // (the table continued periodically to negative indices) with the poison
@@ -194,7 +195,7 @@ constexpr uint32_t kFan2Queue = 16;
 constexpr uint32_t kFan2Prefix = 64;
 constexpr uint32_t kFan2ZeroRow = 8;   // row index L + 8
 struct Fan2Layout {
-    uint32_t us, acc_off, rq_off, sqf_off, bytes;
+    uint32_t us, acc_off, rq_off, sqf_off, par_off, bytes;
 };
 __host__ __device__ inline Fan2Layout fan2_layout(uint32_t q)
 {
@@ -204,7 +205,8 @@ __host__ __device__ inline Fan2Layout fan2_layout(uint32_t q)
     l.acc_off = 4 * l.us;
     l.rq_off = l.acc_off + ((64 * q + 3) & ~3u);
     l.sqf_off = l.rq_off + 2 * kFan2Queue * 32;
-    l.bytes = (l.sqf_off + 4 * nw + 15) & ~15u;
+    l.par_off = (l.sqf_off + 4 * nw + 15) & ~15u;
+    l.bytes = l.par_off + 4 * 64;
     return l;
 }
 inline uint32_t fan2_warp_bytes(uint32_t q) { return fan2_layout(q).bytes; }
