@@ -53,24 +53,34 @@ def evals_per_member(spec: JobSpec) -> int:
     return spec.nominal_evals_per_member()
 
 
-def uses_fanout(spec: JobSpec) -> bool:
-    """The library takes the c_0 fan-out kernel for enumerated families with
-    q <= 63 and the per-member Horner kernel otherwise."""
-    return spec.kind != 2 and spec.q <= 63
+KERNELS = {0: "k_persistent", 1: "k_fan_persistent", 2: "k_fan2_persistent"}
 
 
-def table_reads(spec: JobSpec, n_squarefree: int) -> float:
+def chain_reads(spec: JobSpec, lo: int) -> float:
+    """Expected Zech reads of the shared Horner chain over c_lo..c_d per
+    point: one per nonzero coefficient c_i, lo <= i <= d-1 (c_{d-1} is 0 in
+    the families without the subleading term)."""
+    d, q = spec.degree, spec.q
+    free = d - lo - (1 if spec.kind != 0 else 0)   # positions lo..d-1 that vary
+    return free * (q - 1) / q
+
+
+def table_reads(spec: JobSpec, n_squarefree: int, method: int) -> float:
     """Shared-memory table reads one launch performs for this job (expected
-    value over the family):
-      per-member Horner: one Zech read per nonzero c_i, i <= d-2, per point,
-        (d-1)(q-1)/q per evaluation of a square-free member;
-      c_0 fan-out: per group of q members and point x, one Zech read per
-        nonzero c_i, 1 <= i <= d-2, plus one fan-out row: (d-2)(q-1)/q + 1."""
+    value over the family; points x != 0 of every field F_{q^k}, k <= g):
+      0, per-member Horner: one Zech read per nonzero c_i, i <= d-2, per
+        point of a square-free member;
+      1, fan-out over c_0 (groups of q members): per group and point, the
+        chain over c_1..c_d plus one fan-out row;
+      2, fan-out over (c_1, c_0) (groups of q^2 members): per group and
+        point, the chain over c_2..c_d, one Zech addition per c_1 != 0 and
+        one fan-out row per c_1: chain + 2q - 1."""
     d, q = spec.degree, spec.q
     pts = sum(q ** k - 1 for k in range(1, spec.g + 1))
-    if uses_fanout(spec):
-        groups = spec.n() / q
-        return groups * pts * ((d - 2) * (q - 1) / q + 1)
+    if method == 2:
+        return spec.n() / q ** 2 * pts * (chain_reads(spec, 2) + 2 * q - 1)
+    if method == 1:
+        return spec.n() / q * pts * (chain_reads(spec, 1) + 1)
     return n_squarefree * pts * (d - 1) * (q - 1) / q
 
 
@@ -196,9 +206,11 @@ class ClockSampler:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("count_kernels.cu", "fanout.cuh", "horner.cuh", "count_common.cuh", "hwc_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_1805_11991_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    src = os.path.join(ROOT, "paper_1805_11991_gb300", "csrc")
+    for f in sorted(os.listdir(src)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(src, f), "rb") as fh:
+                h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -256,7 +268,9 @@ def main():
     sqf = [h.n_squarefree for h in results]
     units = sum(n * evals_per_member(s) for n, s in zip(sqf, jobs))
     members = sum(s.n() for s in jobs)
-    lookups = sum(table_reads(s, n) for n, s in zip(sqf, jobs))
+    methods = [batched.job_method(i) for i in range(len(jobs))]
+    lookups = sum(table_reads(s, n, m) for n, s, m in zip(sqf, jobs, methods))
+    kernels = sorted({KERNELS[m] for m in methods})
 
     def timed(batch, k):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
@@ -328,7 +342,7 @@ def main():
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps * batched.kernel_launches(),
         "roofline": {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "Glookup/s",
-                     "frac": achieved / peak, "traffic": traffic, "kernel": "k_fan_persistent" if all(uses_fanout(s) for s in jobs) else "k_persistent",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "+".join(kernels),
                      "kernel_ms": kern_ms,
                      "peak_source": f"{sms} SMs x {sm_max:.0f} MHz x 32 lanes (bank-conflict-free LDS)",
                      "measured_random_gather": measured,

@@ -190,6 +190,12 @@ int hwc_batch_launch(hwc_batch_t *b, void *stream);
 int hwc_batch_result(hwc_batch_t *b, size_t i, hwc_hist_t **out);
 /* Number of kernel launches one hwc_batch_launch enqueues. */
 int hwc_batch_kernel_launches(const hwc_batch_t *b, uint32_t *n);
+/* Count kernel that job i of the batch runs: 0 per-member Horner evaluation
+ * (Algorithm 1 as written), 1 fan-out over c_0 (groups of q members sharing
+ * c_1..c_d), 2 fan-out over (c_1, c_0) (groups of q^2 members).  The choice
+ * is made at hwc_batch_create from the family, q and the shared-memory room
+ * of the field tables (HWC_FLAG_HORNER / HWC_FLAG_FAN1 restrict it). */
+int hwc_batch_job_method(const hwc_batch_t *b, size_t i, uint32_t *method);
 /* Bytes one hwc_batch_launch copies host->device (job descriptors, from
  * pinned memory) and hwc_batch_result copies device->host for all jobs of
  * the last launch (statistics plus the compacted histograms). */

@@ -720,6 +720,14 @@ extern "C" int hwc_batch_kernel_launches(const hwc_batch_t *b, uint32_t *n)
     return HWC_OK;
 }
 
+extern "C" int hwc_batch_job_method(const hwc_batch_t *b, size_t i, uint32_t *method)
+{
+    if (!b || !method) return set_error(HWC_ERR_ARG, "null argument");
+    if (i >= b->pos.size()) return set_error(HWC_ERR_RANGE, "job %zu of %zu", i, b->pos.size());
+    *method = b->jobs[b->pos[i]].kj.method;
+    return HWC_OK;
+}
+
 extern "C" int hwc_batch_io_bytes(const hwc_batch_t *b, uint64_t *h2d, uint64_t *d2h)
 {
     if (!b) return set_error(HWC_ERR_ARG, "batch is NULL");

@@ -87,6 +87,7 @@ def load(build_if_missing: bool = True):
             "hwc_batch_launch": (c_int, [vp, vp]),
             "hwc_batch_result": (c_int, [vp, sz, P(vp)]),
             "hwc_batch_kernel_launches": (c_int, [vp, P(u32)]),
+            "hwc_batch_job_method": (c_int, [vp, ctypes.c_size_t, P(u32)]),
             "hwc_batch_io_bytes": (c_int, [vp, P(u64), P(u64)]),
             "hwc_batch_kernel_ms": (c_int, [vp, P(ctypes.c_float)]),
             "hwc_batch_free": (None, [vp]),
@@ -269,6 +270,12 @@ class Batch:
         n = ctypes.c_uint32()
         _check(_lib.hwc_batch_kernel_launches(self._h, ctypes.byref(n)))
         return n.value
+
+    def job_method(self, i: int) -> int:
+        """Count kernel of job i: 0 Horner, 1 fan-out over c_0, 2 over (c_1, c_0)."""
+        m = ctypes.c_uint32()
+        _check(_lib.hwc_batch_job_method(self._h, i, ctypes.byref(m)))
+        return m.value
 
     def io_bytes(self):
         a, b = ctypes.c_uint64(), ctypes.c_uint64()
