@@ -256,12 +256,14 @@ __device__ void stage_job(const KJob &J, uint8_t *smem)
         uint32_t *dn = reinterpret_cast<uint32_t *>(smem + J.dense_off);
         for (uint32_t i = threadIdx.x; i < J.dense_n; i += blockDim.x) dn[i] = 0;
     }
-    if (J.method != 0) {   // F_q digit arithmetic: mul | sub | inv
+    if (J.method != 0) {   // F_q digit arithmetic: mul | sub | inv | add
         const uint32_t qq = J.q * J.q;
         uint8_t *d = smem + J.fq_off;
         for (uint32_t i = threadIdx.x; i < qq; i += blockDim.x) {
             d[i] = J.fq_mul[i];
             d[qq + i] = J.fq_sub[i];
+            // x + y = x - (0 - y)
+            d[2 * qq + J.q + i] = J.fq_sub[(i / J.q) * J.q + J.fq_sub[i % J.q]];
         }
         for (uint32_t i = threadIdx.x; i < J.q; i += blockDim.x) d[2 * qq + i] = J.fq_inv[i];
     }

@@ -217,41 +217,44 @@ __device__ __forceinline__ void group2_field(const KJob &J, int k, const uint8_t
 // the mul / sub / inv tables.  Returns the mask of square-free c (bit c).
 template <int D>
 __device__ __noinline__ uint32_t sqf_mask_for_b(const uint8_t *mulT, const uint8_t *subT, const uint8_t *invT,
-                                                uint32_t q, uint32_t p, const uint32_t *cg, uint32_t b)
+                                                const uint8_t *addT, uint32_t q, uint32_t p, const uint32_t *cg,
+                                                uint32_t b)
 {
+    // digits fit a byte (q <= 31): byte arrays keep the lane's local
+    // footprint small
     constexpr int MX = D - 1;   // deg w <= D - 1
     auto mul = [&](uint32_t x, uint32_t y) -> uint32_t { return mulT[x * q + y]; };
     auto sub = [&](uint32_t x, uint32_t y) -> uint32_t { return subT[x * q + y]; };
-    auto add = [&](uint32_t x, uint32_t y) -> uint32_t { return subT[x * q + subT[y]]; };   // x - (0 - y)
+    auto add = [&](uint32_t x, uint32_t y) -> uint32_t { return addT[x * q + y]; };
     const uint32_t all = (q >= 32) ? 0xFFFFFFFFu : ((1u << q) - 1u);
     // w = f' = b + sum_{i>=2} (i mod p) c_i x^(i-1)
-    uint32_t w[MX + 1];
-    w[0] = b;
-    for (int i = 2; i <= D; ++i) w[i - 1] = mul(i % p, cg[i]);
+    uint8_t w[MX + 1];
+    w[0] = (uint8_t)b;
+    for (int i = 2; i <= D; ++i) w[i - 1] = (uint8_t)mul(i % p, cg[i]);
     int m = MX;
     while (m >= 0 && w[m] == 0) --m;
     if (m < 0) return 0u;
     if (m == 0) return all;
     const uint32_t wi = invT[w[m]];
-    for (int i = 0; i <= m; ++i) w[i] = mul(w[i], wi);   // monic
+    for (int i = 0; i <= m; ++i) w[i] = (uint8_t)mul(w[i], wi);   // monic
     // r = g_b mod w, g_b = b x + sum_{i>=2} c_i x^i
-    uint32_t r[D + 1];
+    uint8_t r[D + 1];
     r[0] = 0;
-    r[1] = b;
-    for (int i = 2; i <= D; ++i) r[i] = cg[i];
+    r[1] = (uint8_t)b;
+    for (int i = 2; i <= D; ++i) r[i] = (uint8_t)cg[i];
     for (int t = D; t >= m; --t) {
         const uint32_t cf = r[t];
         if (!cf) continue;
         r[t] = 0;
-        for (int i = 0; i < m; ++i) r[t - m + i] = sub(r[t - m + i], mul(cf, w[i]));
+        for (int i = 0; i < m; ++i) r[t - m + i] = (uint8_t)sub(r[t - m + i], mul(cf, w[i]));
     }
     // H[i][j]: coefficient i of g_b x^j mod w
-    uint32_t H[MX][MX];
+    uint8_t H[MX][MX];
     for (int j = 0; j < m; ++j) {
         for (int i = 0; i < m; ++i) H[i][j] = r[i];
         const uint32_t top = r[m - 1];
-        for (int i = m - 1; i >= 1; --i) r[i] = sub(r[i - 1], mul(top, w[i]));
-        r[0] = sub(0, mul(top, w[0]));
+        for (int i = m - 1; i >= 1; --i) r[i] = (uint8_t)sub(r[i - 1], mul(top, w[i]));
+        r[0] = (uint8_t)sub(0, mul(top, w[0]));
     }
     // upper Hessenberg form by similarity
     for (int j = 0; j + 2 < m; ++j) {
@@ -260,40 +263,40 @@ __device__ __noinline__ uint32_t sqf_mask_for_b(const uint8_t *mulT, const uint8
             if (H[i][j]) { piv = i; break; }
         if (piv < 0) continue;
         if (piv != j + 1) {
-            for (int k = 0; k < m; ++k) { const uint32_t t = H[piv][k]; H[piv][k] = H[j + 1][k]; H[j + 1][k] = t; }
-            for (int k = 0; k < m; ++k) { const uint32_t t = H[k][piv]; H[k][piv] = H[k][j + 1]; H[k][j + 1] = t; }
+            for (int k = 0; k < m; ++k) { const uint8_t t = H[piv][k]; H[piv][k] = H[j + 1][k]; H[j + 1][k] = t; }
+            for (int k = 0; k < m; ++k) { const uint8_t t = H[k][piv]; H[k][piv] = H[k][j + 1]; H[k][j + 1] = t; }
         }
         const uint32_t iv = invT[H[j + 1][j]];
         for (int i = j + 2; i < m; ++i) {
             if (!H[i][j]) continue;
             const uint32_t f = mul(H[i][j], iv);
-            for (int k = 0; k < m; ++k) H[i][k] = sub(H[i][k], mul(f, H[j + 1][k]));
-            for (int k = 0; k < m; ++k) H[k][j + 1] = add(H[k][j + 1], mul(f, H[k][i]));
+            for (int k = 0; k < m; ++k) H[i][k] = (uint8_t)sub(H[i][k], mul(f, H[j + 1][k]));
+            for (int k = 0; k < m; ++k) H[k][j + 1] = (uint8_t)add(H[k][j + 1], mul(f, H[k][i]));
         }
     }
     // p_k(t) = (t - h_kk) p_{k-1} - sum_{i<k} h_ik (prod_{j=i+1..k} h_{j,j-1}) p_{i-1}  (1-based)
-    uint32_t P[MX + 1][MX + 1];
+    uint8_t P[MX + 1][MX + 1];
     P[0][0] = 1;
     for (int k = 1; k <= m; ++k) {
         for (int e = 0; e <= k; ++e) {   // (t - h_kk) p_{k-1}
             uint32_t v = (e >= 1) ? P[k - 1][e - 1] : 0u;
             if (e <= k - 1) v = sub(v, mul(H[k - 1][k - 1], P[k - 1][e]));
-            P[k][e] = v;
+            P[k][e] = (uint8_t)v;
         }
         uint32_t prod = 1;
         for (int i = k - 1; i >= 1; --i) {
             prod = mul(prod, H[i][i - 1]);            // h_{i+1,i} (1-based)
             const uint32_t f = mul(H[i - 1][k - 1], prod);
             if (!f) continue;
-            for (int e = 0; e <= i - 1; ++e) P[k][e] = sub(P[k][e], mul(f, P[i - 1][e]));
+            for (int e = 0; e <= i - 1; ++e) P[k][e] = (uint8_t)sub(P[k][e], mul(f, P[i - 1][e]));
         }
     }
-    // member c square-free iff chi(-c) != 0
+    // member c square-free iff chi(-c) != 0; chi is monic of degree m
     uint32_t mask = 0;
     for (uint32_t c = 0; c < q; ++c) {
-        const uint32_t t = sub(0, c);
-        uint32_t v = P[m][m];
-        for (int e = m - 1; e >= 0; --e) v = add(mul(v, t), P[m][e]);
+        const uint8_t *mrow = mulT + subT[c] * q;   // times t = -c
+        uint32_t v = 1;
+        for (int e = m - 1; e >= 0; --e) v = addT[mrow[v] * q + P[m][e]];
         if (v) mask |= 1u << c;
     }
     return mask;
@@ -317,7 +320,9 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
 
     // per-warp shared scratch (fan2_layout); the members' keys live in this
     // warp's slot of global scratch
-    const Fan2Layout lay = fan2_layout(q);
+    const Fan2Layout lay = fan2_layout(q, J.dense_off != 0);
+    uint16_t *a1s = reinterpret_cast<uint16_t *>(wsm + lay.a1_off);   // dense histogram: a_1 + 32768
+    uint32_t *dense = reinterpret_cast<uint32_t *>(const_cast<uint8_t *>(smem) + J.dense_off);
     uint32_t *Us = reinterpret_cast<uint32_t *>(wsm);
     uint16_t *acc = reinterpret_cast<uint16_t *>(wsm + lay.acc_off);
     uint16_t *rq = reinterpret_cast<uint16_t *>(wsm + lay.rq_off);
@@ -335,6 +340,7 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
     const uint8_t *mulT = smem + J.fq_off;
     const uint8_t *subT = mulT + qq;
     const uint8_t *invT = subT + qq;
+    const uint8_t *addT = invT + q;
 
     // square-freeness: lane b settles the q members with c_1 = b at once
     for (uint32_t t = lane; t < nw; t += 32) sqfw[t] = 0;
@@ -345,7 +351,7 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
     }
     __syncwarp();
     if ((uint32_t)lane < q) {
-        const uint32_t mask = sqf_mask_for_b<D>(mulT, subT, invT, q, J.p, gc, (uint32_t)lane);
+        const uint32_t mask = sqf_mask_for_b<D>(mulT, subT, invT, addT, q, J.p, gc, (uint32_t)lane);
         // bits b*q .. b*q + q-1 of the member mask
         const uint32_t bit0 = (uint32_t)lane * q;
         const uint32_t w0 = bit0 >> 5, sh = bit0 & 31u;
@@ -441,32 +447,31 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
                     }
                 }
                 const int a = (int)Q + 1 - N;   // eq. 1.1
-                const unsigned long long part = (unsigned long long)((uint32_t)(a + 32768) & 0xFFFFu) << (16 * k);
-                if (k == 0) keys[m] = part;
-                else keys[m] |= part;
+                const uint32_t a16 = (uint32_t)(a + 32768) & 0xFFFFu;
+                if (J.dense_off) {
+                    // g <= 2: a_1 waits in shared memory; the last field counts the member
+                    if (k + 1 < G) {
+                        a1s[m] = (uint16_t)a16;
+                    } else if (!J.member_counts && ((sqfw[m / 32] >> (m % 32)) & 1u)) {
+                        const uint32_t k1 = G == 2 ? a1s[m] : a16;
+                        const int i1 = (int)k1 - 32768 + J.dense_b1;
+                        const int i2 = G == 2 ? a + J.dense_b2 : 0;
+                        if (i1 >= 0 && i1 <= 2 * J.dense_b1 && i2 >= 0 && i2 <= 2 * J.dense_b2)
+                            atomicAdd(&dense[(uint32_t)i1 * J.dense_w2 + (uint32_t)i2], 1u);
+                        else   // outside the Hasse-Weil box: not for a smooth curve
+                            hist_insert(J, G == 2 ? ((unsigned long long)a16 << 16 | k1) : a16, 1u);
+                    }
+                } else {
+                    const unsigned long long part = (unsigned long long)a16 << (16 * k);
+                    if (k == 0) keys[m] = part;
+                    else keys[m] |= part;
+                }
             }
         }
         __syncwarp();
     }
-    if (J.member_counts) return;
+    if (J.member_counts || J.dense_off) return;   // dense: counted with the last field
     __syncwarp();
-    if (J.dense_off) {   // g <= 2: the CTA's shared (a_1, a_2) counters
-        uint32_t *dense = reinterpret_cast<uint32_t *>(const_cast<uint8_t *>(smem) + J.dense_off);
-        for (uint32_t t = 0; t < nw; ++t) {
-            const uint32_t m = t * 32 + lane;
-            if (m < qq && ((sqfw[t] >> lane) & 1u)) {
-                const unsigned long long key = keys[m];
-                const int i1 = (int)(key & 0xFFFFu) - 32768 + J.dense_b1;
-                const int i2 = G == 2 ? (int)((key >> 16) & 0xFFFFu) - 32768 + J.dense_b2 : 0;
-                if (i1 >= 0 && i1 <= 2 * J.dense_b1 && i2 >= 0 && i2 <= 2 * J.dense_b2)
-                    atomicAdd(&dense[(uint32_t)i1 * J.dense_w2 + (uint32_t)i2], 1u);
-                else
-                    hist_insert(J, key, 1u);   // outside the Hasse-Weil box: not for a smooth curve
-            }
-        }
-        __syncwarp();
-        return;
-    }
     for (uint32_t t = 0; t < nw; ++t) {
         const uint32_t m = t * 32 + lane;
         const bool sq = m < qq && ((sqfw[t] >> lane) & 1u);

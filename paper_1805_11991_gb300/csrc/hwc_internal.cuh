@@ -121,7 +121,7 @@ struct KJob {
     unsigned long long *wkeys;        // per-warp member keys in global memory (method 2):
     uint32_t wkeys_stride, pad3;      //   slot blockIdx.x * warps + warp, stride q^2
     const uint8_t *fq_mul, *fq_sub, *fq_inv;   // digit arithmetic of F_q (fan-out jobs)
-    uint32_t fq_off;                  // byte offset of mul | sub | inv in smem
+    uint32_t fq_off;                  // byte offset of mul | sub | inv | add in smem
     // outputs
     unsigned long long *hkeys;        // [hmask+1]
     unsigned long long *hcounts;      // [hmask+1]
@@ -187,6 +187,7 @@ constexpr int kFan2WarpsHost = 4;   // warps per CTA of the two-level kernel
 //   rq[16][32] u16: per-lane queue of row indices with a zero digit
 //   sqf[ceil(q^2/32)] u32: square-free member bits
 //   par[64] u32: the group's digits c_i, the field's logs lam_i and h chain
+//   a1[q^2] u16 (dense histogram only): a_1 + 32768 of every member
 constexpr uint32_t kFan2Queue = 16;
 // The two-level kernel stages each Zech table behind a prefix of 64 entries
 // (the table continued periodically to negative indices) with the poison
@@ -195,9 +196,9 @@ constexpr uint32_t kFan2Queue = 16;
 constexpr uint32_t kFan2Prefix = 64;
 constexpr uint32_t kFan2ZeroRow = 8;   // row index L + 8
 struct Fan2Layout {
-    uint32_t us, acc_off, rq_off, sqf_off, par_off, bytes;
+    uint32_t us, acc_off, rq_off, sqf_off, par_off, a1_off, bytes;
 };
-__host__ __device__ inline Fan2Layout fan2_layout(uint32_t q)
+__host__ __device__ inline Fan2Layout fan2_layout(uint32_t q, bool dense)
 {
     Fan2Layout l;
     const uint32_t S = 32 / q, nw = (q * q + 31) / 32;
@@ -206,10 +207,11 @@ __host__ __device__ inline Fan2Layout fan2_layout(uint32_t q)
     l.rq_off = l.acc_off + ((64 * q + 3) & ~3u);
     l.sqf_off = l.rq_off + 2 * kFan2Queue * 32;
     l.par_off = (l.sqf_off + 4 * nw + 15) & ~15u;
-    l.bytes = l.par_off + 4 * 64;
+    l.a1_off = l.par_off + 4 * 64;
+    l.bytes = (l.a1_off + (dense ? 2 * q * q : 0) + 15) & ~15u;
     return l;
 }
-inline uint32_t fan2_warp_bytes(uint32_t q) { return fan2_layout(q).bytes; }
+inline uint32_t fan2_warp_bytes(uint32_t q, bool dense) { return fan2_layout(q, dense).bytes; }
 // launch shape of the two-level kernel for jobs with these smem needs: the
 // block (4, 8, 16 or 24 warps) that keeps most warps resident; *smem receives the
 // dynamic shared memory of that block

@@ -130,8 +130,8 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit)
         if (j.method == 0) return 0;
         uint64_t b = 0;
         for (uint32_t k = 0; k < j.g; ++k) b += ((row_bytes(k) + 15) / 16) * 16 + ((j.q + 15) / 16) * 16;
-        b += ((2ull * j.q * j.q + j.q + 15) / 16) * 16;
-        if (j.method == 2) b += 16 + (uint64_t)kFan2WarpsHost * fan2_warp_bytes(j.q);   // smallest block
+        b += ((3ull * j.q * j.q + j.q + 15) / 16) * 16;
+        if (j.method == 2) b += 16 + (uint64_t)kFan2WarpsHost * fan2_warp_bytes(j.q, false);   // smallest block
         return b;
     };
     auto bytes_for = [&](void) {
@@ -142,7 +142,7 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit)
     // the two-level kernel reads its Zech tables only in the shared chain: give
     // up tripled tables, largest first, while that makes room for 16 warps
     if (j.method == 2) {
-        const uint64_t extra = (uint64_t)(16 - kFan2WarpsHost) * fan2_warp_bytes(j.q);
+        const uint64_t extra = (uint64_t)(16 - kFan2WarpsHost) * fan2_warp_bytes(j.q, false);
         while (bytes_for() + extra > smem_limit) {
             int big = -1;
             for (uint32_t k = 0; k < j.g; ++k)
@@ -187,7 +187,7 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit)
         }
     }
     j.fq_off = bytes;
-    if (j.method != 0) bytes += ((2 * j.q * j.q + j.q + 15) / 16) * 16;
+    if (j.method != 0) bytes += ((3 * j.q * j.q + j.q + 15) / 16) * 16;   // mul | sub | inv | add
     j.warp_off = 0;
     j.warp_bytes = 0;
     j.dense_off = 0;
@@ -200,7 +200,7 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit)
             const int32_t b2 = j.g == 2 ? (int32_t)(2 * j.g * j.q) : 0;
             const uint32_t n = (uint32_t)(2 * b1 + 1) * (uint32_t)(2 * b2 + 1);
             const uint32_t dbytes = (4 * n + 15) / 16 * 16;
-            if ((uint64_t)bytes + dbytes + 24ull * fan2_warp_bytes(j.q) + 16 <= smem_limit) {
+            if ((uint64_t)bytes + dbytes + 24ull * fan2_warp_bytes(j.q, true) + 16 <= smem_limit) {
                 j.dense_off = bytes;
                 j.dense_b1 = b1;
                 j.dense_b2 = b2;
@@ -210,7 +210,7 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit)
             }
         }
         j.warp_off = bytes;
-        j.warp_bytes = fan2_warp_bytes(j.q);
+        j.warp_bytes = fan2_warp_bytes(j.q, j.dense_off != 0);
         bytes += kFan2WarpsHost * j.warp_bytes;
     }
     j.smem_bytes = bytes;
