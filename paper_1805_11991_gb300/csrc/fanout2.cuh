@@ -116,10 +116,8 @@ __device__ __forceinline__ void fan2_block(const Tab T, const uint32_t *__restri
 #pragma unroll
     for (int v = 0; v < 8; ++v) {
         if (GEN && !((okm >> v) & 1u)) a[v] = 0u;
-        if ((int)a[v] < 0) {   // flagged: y in F_q
-            rq[qn] = (uint16_t)ly[v];
-            qn += 32;
-        }
+        rq[qn] = (uint16_t)ly[v];    // kept when flagged (y in F_q): no branch
+        qn += (a[v] >> 31) << 5;
     }
 }
 
