@@ -74,7 +74,7 @@ __device__ __forceinline__ void drain_queue(const uint16_t *rq, uint32_t qn, int
         uint32_t l = rq[i];
         uint32_t d = 0;
         if (l != L + kFan2ZeroRow) {
-            if (l >= L) l %= L;
+            while (l >= L) l -= L;   // wrapped rows: once for L >= 8
             d = zdig[zdiv ? __umulhi(l, zdiv) : l];
         }
         acc_row[d] = (uint16_t)(acc_row[d] + 1);
