@@ -70,14 +70,17 @@ __device__ __forceinline__ void flush_planes(uint32_t (&P)[kFan2Planes], uint16_
 __device__ __forceinline__ void drain_queue(const uint16_t *rq, uint32_t qn, int lane, const uint8_t *zdig,
                                             uint32_t zdiv, uint32_t L, uint16_t *acc_row)
 {
+    // selects, no branches in the body
+    const uint32_t zrow = L + kFan2ZeroRow;
     for (uint32_t i = (uint32_t)lane; i < qn; i += 32) {
         uint32_t l = rq[i];
-        uint32_t d = 0;
-        if (l != L + kFan2ZeroRow) {
-            while (l >= L) l -= L;   // wrapped rows: once for L >= 8
-            d = zdig[zdiv ? __umulhi(l, zdiv) : l];
-        }
-        acc_row[d] = (uint16_t)(acc_row[d] + 1);
+        const bool zr = l == zrow;
+        if (L >= kFan2ZeroRow) l = min(l, l - L);   // rows [L, L + 8) stand for l - L
+        else l %= L;                               // fields of fewer than 8 nonzero elements
+        // in bounds for zr too: index <= 8 < 16 <= zdig bytes
+        const uint32_t d = zdig[zdiv ? __umulhi(l, zdiv) : l];
+        const uint32_t di = zr ? 0u : d;
+        acc_row[di] = (uint16_t)(acc_row[di] + 1);
     }
 }
 
