@@ -178,9 +178,18 @@ void hwc_hist_free(hwc_hist_t *h);
 
 /* Prepare a batch: builds (or reuses) the field tables of every job,
  * allocates one device histogram per job and the work queue, and picks the
- * kernel parameters (autotuned unless HWC_FLAG_NO_TUNE).  With HWC_FLAG_PLAIN
- * each job gets its own launch instead of one persistent launch.  With
- * HWC_FLAG_GRAPH the launch sequence is captured once in a CUDA graph. */
+ * kernel parameters.  Unless HWC_FLAG_NO_TUNE, the autotuner times the
+ * candidate choices for each class of jobs (g, q, degree, family kind) the
+ * first time the class is seen, on a probe slice of that job (about two work
+ * items per resident warp; smaller jobs keep the default rule): the kernel
+ * (per-member evaluation, or fan-out over c_0 or (c_1, c_0)), the warps per
+ * CTA and the layout of the shared Zech tables.  It launches probe kernels on
+ * the legacy default stream before returning.  Choices are cached per
+ * process, and in the file named by the environment variable HWC_TUNE_CACHE
+ * when it is set.  Every choice gives the same histograms.  With
+ * HWC_FLAG_PLAIN each job gets its own launch instead of one persistent
+ * launch.  With HWC_FLAG_GRAPH the launch sequence is captured once in a
+ * CUDA graph. */
 int hwc_batch_create(const hwc_job_t *jobs, size_t n_jobs, uint32_t flags,
                      hwc_batch_t **out);
 /* Enqueue one complete run of the batch on `stream` (asynchronous): clears

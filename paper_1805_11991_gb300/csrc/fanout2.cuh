@@ -119,8 +119,10 @@ __device__ __forceinline__ void fan2_block(const Tab T, const uint32_t *__restri
 #pragma unroll
     for (int v = 0; v < 8; ++v) {
         if (GEN && !((okm >> v) & 1u)) a[v] = 0u;
-        rq[qn] = (uint16_t)ly[v];    // kept when flagged (y in F_q): no branch
-        qn += (a[v] >> 31) << 5;
+        if ((int)a[v] < 0) {   // flagged: y in F_q (rare for k >= 3)
+            rq[qn] = (uint16_t)ly[v];
+            qn += 32;
+        }
     }
 }
 

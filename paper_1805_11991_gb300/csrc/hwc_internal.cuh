@@ -156,9 +156,23 @@ int device_sm_count(void);
 uint32_t device_smem_optin(void);
 
 // fills the job's smem layout (tab_off, coef_off, row_off, smem_bytes)
-bool layout_job_smem(KJob &j, uint32_t smem_limit);
+// A kernel choice for one class of jobs (g, q, degree, family kind), made by
+// the autotuner (tune.cu) or left to the default rule.
+struct TuneChoice {
+    int method = -1;          // -1: default rule; 0 per member, 1 c_0 fan-out, 2 (c_1, c_0) fan-out
+    int warps = 0;            // two-level kernel: warps per CTA (0: the most resident)
+    bool no_triple = false;   // shared Zech tables in the doubled layout only
+};
+bool layout_job_smem(KJob &j, uint32_t smem_limit, bool no_triple = false);
 // validates a job and fills a KJob (tables, method, layout); outputs left null
-int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n, uint32_t flags);
+int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n, uint32_t flags, const TuneChoice *tc = nullptr);
+// autotuner: the fastest measured choice for the job's class (measured on a
+// probe slice the first time a class is seen, then cached per process and,
+// with HWC_TUNE_CACHE set, in that file); tune_lookup only reads the cache
+int tune_choice(const hwc_job_t &jb, uint32_t flags, TuneChoice *out);
+bool tune_lookup(const hwc_job_t &jb, uint32_t flags, TuneChoice *out);
+// a batch whose jobs take the given choices (no autotuning); for probes
+int batch_create_with(const hwc_job_t *jobs, size_t n, uint32_t flags, const TuneChoice *tc, hwc_batch **out);
 // launch shape for a kernel (degree, method, row words) at this much dynamic smem
 int choose_shape(int D, uint32_t method, uint32_t words, uint32_t smem, bool persistent, LaunchShape *out);
 // kernel entry points by degree: which = 1 persistent, 2 allocation-free
@@ -218,7 +232,7 @@ inline uint32_t fan2_warp_bytes(uint32_t q, bool dense) { return fan2_layout(q, 
 struct Fan2Need {
     uint32_t warp_off, warp_bytes;
 };
-int choose_shape_fan2(int D, const Fan2Need *needs, size_t n, LaunchShape *out, uint32_t *smem);
+int choose_shape_fan2(int D, const Fan2Need *needs, size_t n, LaunchShape *out, uint32_t *smem, int warps = 0);
 const void *fan_kernel_e(int D, int W, bool persistent);   // fanout_e.cu, D = 9, 10
 // hash slots for a job of `count` members (power of two)
 uint32_t hash_capacity(uint32_t g, uint32_t q, uint64_t count, uint32_t scale);

@@ -104,11 +104,11 @@ static uint64_t isqrt_u64(uint64_t v)   // floor(sqrt(v))
     return x;
 }
 
-bool layout_job_smem(KJob &j, uint32_t smem_limit)
+bool layout_job_smem(KJob &j, uint32_t smem_limit, bool no_triple)
 {
     uint32_t kind[kMaxG];
     for (uint32_t k = 0; k < j.g; ++k)
-        kind[k] = j.zech3[k] ? kTabTripleSmem : (j.zech2[k] ? kTabDoubleSmem : kTabDoubleGlobal);
+        kind[k] = (j.zech3[k] && !no_triple) ? kTabTripleSmem : (j.zech2[k] ? kTabDoubleSmem : kTabDoubleGlobal);
     // the two-level kernel's lanes b read Zech entries log b apart: multiples
     // of s = L/(q-1).  For s = 0 mod 4 those fall on few banks unless the
     // table carries one pad word per 32.
@@ -241,9 +241,10 @@ struct HostJob {
     hwc_job_t job;
     KJob kj;
     uint64_t fam_n;
+    int warps = 0;   // tuned warps per CTA (two-level kernel)
 };
 
-int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n, uint32_t flags)
+int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n, uint32_t flags, const TuneChoice *tc)
 {
     int rc = validate_job(jb, fam_n);
     if (rc) return rc;
@@ -262,7 +263,9 @@ int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n, uint32_t flags)
     kj.qd = kj.fam_mz * jb.q;
     kj.n_tiles = (jb.count + kTileMembers - 1) / kTileMembers;
     // enumerated families with q <= 63: groups of q members share all but c_0
-    const bool fan = !(flags & HWC_FLAG_HORNER) && jb.family.kind != HWC_FAM_MONIC_NOSUB_SAMPLED && jb.q <= 63;
+    const bool fan = !(flags & HWC_FLAG_HORNER) && jb.family.kind != HWC_FAM_MONIC_NOSUB_SAMPLED && jb.q <= 63 &&
+                     !(tc && tc->method == 0);
+    const bool no_triple = tc && tc->no_triple;
     // (method chosen below: two-level fan-out for q <= 31, one-level up to 63,
     // per-member Horner otherwise or when a layout does not fit)
     for (uint32_t k = 1; k <= jb.g; ++k) {
@@ -289,26 +292,26 @@ int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n, uint32_t flags)
         kj.zdiv[k - 1] = sdiv == 1 ? 0u : (uint32_t)(((1ull << 32) + sdiv - 1) / sdiv);
     }
     const uint32_t limit = device_smem_optin() - 4096;   // static smem of the kernels
-    if (fan && jb.q <= 31 && !(flags & HWC_FLAG_FAN1)) {
+    if (fan && jb.q <= 31 && !(flags & HWC_FLAG_FAN1) && !(tc && tc->method == 1)) {
         // two-level fan-out: groups of q^2 members
         kj.method = 2;
         kj.words = 1;
         kj.first_group = jb.first / ((uint64_t)jb.q * jb.q);
         kj.n_tiles = jb.count ? (jb.first + jb.count - 1) / ((uint64_t)jb.q * jb.q) - kj.first_group + 1 : 0;
-        if (layout_job_smem(kj, limit)) return HWC_OK;
+        if (layout_job_smem(kj, limit, no_triple)) return HWC_OK;
     }
     if (fan) {
         kj.method = 1;
         kj.words = jb.q <= 31 ? 1 : 2;
         kj.first_group = jb.first / jb.q;
         kj.n_tiles = jb.count ? (jb.first + jb.count - 1) / jb.q - kj.first_group + 1 : 0;
-        if (layout_job_smem(kj, limit)) return HWC_OK;
+        if (layout_job_smem(kj, limit, no_triple)) return HWC_OK;
         kj.method = 0;   // rows do not fit: per-member Horner
         kj.words = 0;
         kj.first_group = 0;
         kj.n_tiles = (jb.count + kTileMembers - 1) / kTileMembers;
     }
-    layout_job_smem(kj, limit);
+    layout_job_smem(kj, limit, no_triple);
     return HWC_OK;
 }
 
@@ -379,6 +382,8 @@ hwc_hist *hwc::hist_from_keys(const KJob &kj, const unsigned long long *keys,
 struct BatchGroup {
     int D = 0;
     uint32_t method = 0, words = 0;
+    int warps = 0;                   // tuned warps per CTA (two-level kernel)
+    uint64_t warps_tiles = 0;        // groups of the job that set `warps`
     uint32_t first = 0, n = 0;       // jobs[first .. first+n) (sorted by degree)
     uint32_t start_off = 0;          // offset of this group's item table
     uint64_t n_items = 0;
@@ -484,12 +489,13 @@ int hwc::choose_shape(int D, uint32_t method, uint32_t words, uint32_t smem, boo
     return HWC_OK;
 }
 
-int hwc::choose_shape_fan2(int D, const Fan2Need *needs, size_t n, LaunchShape *out, uint32_t *smem)
+int hwc::choose_shape_fan2(int D, const Fan2Need *needs, size_t n, LaunchShape *out, uint32_t *smem, int warps)
 {
     const int sms = device_sm_count();
     const uint32_t limit = device_smem_optin() - 4096;
     int best_warps = -1;
     for (int block : {768, 512, 256, 128}) {
+        if (warps > 0 && block != 32 * warps) continue;   // the tuned block
         const uint32_t W = (uint32_t)block / 32;
         uint32_t need = 0;
         for (size_t i = 0; i < n; ++i) need = std::max(need, needs[i].warp_off + W * needs[i].warp_bytes);
@@ -505,12 +511,15 @@ int hwc::choose_shape_fan2(int D, const Fan2Need *needs, size_t n, LaunchShape *
             *smem = need;
         }
     }
-    if (best_warps <= 0) return set_error(HWC_ERR_TOO_LARGE, "no CTA of the two-level kernel fits");
+    if (best_warps <= 0) {
+        if (warps > 0) return choose_shape_fan2(D, needs, n, out, smem, 0);   // the tuned block no longer fits
+        return set_error(HWC_ERR_TOO_LARGE, "no CTA of the two-level kernel fits");
+    }
     return HWC_OK;
 }
 
 static int batch_create_impl(const hwc_job_t *jobs, size_t n, uint32_t flags, uint32_t cap_scale,
-                             hwc_batch **out)
+                             hwc_batch **out, const TuneChoice *given = nullptr)
 {
     *out = nullptr;
     if (!jobs || n == 0) return set_error(HWC_ERR_ARG, "no jobs");
@@ -529,8 +538,16 @@ static int batch_create_impl(const hwc_job_t *jobs, size_t n, uint32_t flags, ui
     std::vector<HostJob> filled(n);
     for (size_t i = 0; i < n; ++i) {
         filled[i].job = jobs[i];
-        rc = fill_kjob(jobs[i], filled[i].kj, &filled[i].fam_n, flags);
+        TuneChoice tc;
+        if (given) {
+            tc = *given;
+        } else if (!(flags & HWC_FLAG_NO_TUNE)) {
+            rc = tune_choice(jobs[i], flags, &tc);
+            if (rc) { batch_release(b); return rc; }
+        }
+        rc = fill_kjob(jobs[i], filled[i].kj, &filled[i].fam_n, flags, &tc);
         if (rc) { batch_release(b); return rc; }
+        filled[i].warps = tc.warps;
     }
     std::vector<size_t> order(n);
     std::iota(order.begin(), order.end(), 0);
@@ -568,6 +585,12 @@ static int batch_create_impl(const hwc_job_t *jobs, size_t n, uint32_t flags, ui
         BatchGroup &G = b->groups.back();
         G.n++;
         G.max_smem = std::max(G.max_smem, kj.smem_bytes);
+        // warps per CTA are a property of the launch: the tuned value of the
+        // group's largest job
+        if (kj.method == 2 && kj.n_tiles >= G.warps_tiles) {
+            G.warps_tiles = kj.n_tiles;
+            G.warps = hj.warps;
+        }
     }
     const bool persistent = !(flags & HWC_FLAG_PLAIN);
     std::vector<uint64_t> starts;
@@ -579,7 +602,7 @@ static int batch_create_impl(const hwc_job_t *jobs, size_t n, uint32_t flags, ui
                 needs.push_back({b->jobs[r].kj.warp_off, b->jobs[r].kj.warp_bytes});
                 max_qq = std::max(max_qq, b->jobs[r].kj.q * b->jobs[r].kj.q);
             }
-            if ((rc = choose_shape_fan2(G.D, needs.data(), needs.size(), &G.shape, &G.max_smem))) {
+            if ((rc = choose_shape_fan2(G.D, needs.data(), needs.size(), &G.shape, &G.max_smem, G.warps))) {
                 batch_release(b);
                 return rc;
             }
@@ -684,6 +707,12 @@ static int batch_result_impl(hwc_batch *b, size_t i, hwc_hist **out)
     }
     *out = h;
     return HWC_OK;
+}
+
+int hwc::batch_create_with(const hwc_job_t *jobs, size_t n, uint32_t flags, const TuneChoice *tc,
+                           hwc_batch **out)
+{
+    return batch_create_impl(jobs, n, flags | HWC_FLAG_NO_TUNE, 1, out, tc);
 }
 
 extern "C" int hwc_batch_create(const hwc_job_t *jobs, size_t n_jobs, uint32_t flags, hwc_batch_t **out)
