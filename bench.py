@@ -46,6 +46,11 @@ def parse():
     ap.add_argument("--config", default="config2", choices=sorted(CONFIGS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--serve", action="store_true",
+                    help="also run the served form: the workload cut into requests on a Poisson schedule")
+    ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serve-load", type=float, default=0.8,
+                    help="offered load as a fraction of the measured batched throughput")
     return ap.parse_args()
 
 
@@ -228,6 +233,62 @@ def profiled_traffic():
 
 
 # ---------------------------------------------------------------------------
+# served form
+
+def serve_leg(hwc, jobs, batched_results, batched_evals_per_s, n_requests, load, seed=11):
+    """The workload as a stream of requests: every job cut into slices of about
+    equal evaluation work, shuffled (seed), submitted at Poisson arrival times
+    (seed) whose mean rate offers `load` times the batched throughput.  Returns
+    throughput, p50/p99 latency (submit -> result) and whether every job's
+    merged slices equal its batched histogram."""
+    import numpy as np
+    from paper_1805_11991_gb300.workloads import poisson_arrivals, split_job
+    work = [s.n() * evals_per_member(s) for s in jobs]
+    target = sum(work) / n_requests
+    reqs = []
+    for j, (spec, w) in enumerate(zip(jobs, work)):
+        reqs += [(j, r) for r in split_job(spec, max(1, round(w / target)))]
+    order = np.random.default_rng(seed).permutation(len(reqs))
+    reqs = [reqs[i] for i in order]
+    req_evals = [r.n() * evals_per_member(r) for _, r in reqs]
+    mean_service_s = (sum(req_evals) / len(reqs)) / batched_evals_per_s
+    arrivals = poisson_arrivals(len(reqs), load / mean_service_s, seed=seed)
+    srv = hwc.Server()
+    tickets, submitted = [], []
+    t0 = time.perf_counter()
+    for (j, r), t_arr in zip(reqs, arrivals):
+        delay = t0 + float(t_arr) - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        submitted.append(time.perf_counter())
+        tickets.append(srv.submit(hwc.make_job(r.g, r.q, r.kind, r.degree, r.first, r.n(), r.seed,
+                                               r.sample_count)))
+    hists = []
+    for t in tickets:
+        h = None
+        while h is None:
+            h = srv.poll(t, 1000)
+        hists.append(h)
+    total_ms = [srv.latency(t)[1] / 1e3 for t in tickets]    # submit -> done, from the server's clock
+    srv.close()
+    # wall time: first submission to the last request done (host-side merging excluded)
+    t_end = max(sub + ms / 1e3 for sub, ms in zip(submitted, total_ms))
+    sqf = sum(h.n_squarefree * evals_per_member(r) for h, (_, r) in zip(hists, reqs))
+    lat = sorted(total_ms)
+    merged = [None] * len(jobs)
+    for h, (j, _) in zip(hists, reqs):
+        merged[j] = h if merged[j] is None else hwc.hist_merge(merged[j], h)
+    same = all(m is not None and np.array_equal(m.counts, b.counts) and np.array_equal(m.mult, b.mult)
+               for m, b in zip(merged, batched_results))
+    p = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))]
+    return {"value": sqf / (t_end - t0), "unit": UNIT, "requests": len(reqs),
+            "arrival_rate_per_s": load / mean_service_s, "offered_load": load,
+            "p50_ms": p(0.50), "p99_ms": p(0.99), "max_ms": lat[-1], "wall_s": t_end - t0,
+            "arrivals": "Poisson, seed %d; requests: every job cut into slices of equal work, shuffled" % seed,
+            "matches_batched": bool(same)}
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 
 def main():
@@ -352,6 +413,8 @@ def main():
         r, c, threads, sample = oracle_rate(jobs, args.cpu_seconds)
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": sample, "curves_per_s": c}
+    if args.serve and rank == 0:
+        line["served"] = serve_leg(hwc, jobs, results, value / world, args.serve_requests, args.serve_load)
     line["clocks"] = clk.summary()
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -229,9 +229,11 @@ void server_loop(hwc_server *s)
                 rc = shape_for(s, G.D, G.method, G.words, smem, &G.sh);
             }
             if (rc) break;
-            uint64_t budget = s->cfg.step_items ? s->cfg.step_items : (uint64_t)G.sh.grid * 4;
+            // per launch: about 8 work items per CTA (the tail of a launch weighs
+            // little), shared evenly by the group's requests
+            uint64_t budget = s->cfg.step_items ? s->cfg.step_items : (uint64_t)G.sh.grid * 8;
             budget *= (uint64_t)G.sh.item_tiles;
-            const uint64_t share = std::max<uint64_t>(G.sh.item_tiles, budget / n);
+            const uint64_t share = std::max<uint64_t>(G.sh.item_tiles, budget / (e - i));
             uint64_t items = 0;
             for (uint32_t r = i; r < e; ++r) {
                 Request *q = step[r];
