@@ -267,6 +267,10 @@ __device__ void stage_job(const KJob &J, uint8_t *smem)
         }
         for (uint32_t i = threadIdx.x; i < J.q; i += blockDim.x) d[2 * qq + i] = J.fq_inv[i];
     }
+    if (J.coord_off) {   // coordinates of F_{q^2} over F_q (two-level kernel)
+        uint32_t *d = reinterpret_cast<uint32_t *>(smem + J.coord_off);
+        for (uint32_t i = threadIdx.x; i < J.L[1]; i += blockDim.x) d[i] = J.coord2[i];
+    }
 }
 
 __device__ __forceinline__ void flush_stats(const KJob &J, WarpStats &st, int lane)

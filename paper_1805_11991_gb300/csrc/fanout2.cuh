@@ -84,6 +84,64 @@ __device__ __forceinline__ void drain_queue(const uint16_t *rq, uint32_t qn, int
     }
 }
 
+// z(b, c) += 1 in the group's accumulator rows (row b of chunk 0, column c):
+// one shared atomic on the u32 word that holds the u16 entry
+__device__ __forceinline__ void zinc(uint32_t *acc32, uint32_t q, uint32_t b, uint32_t c)
+{
+    const uint32_t i = b * q + c;
+    atomicAdd(acc32 + (i >> 1), 1u << ((i & 1u) << 4));
+}
+
+// Zero digits of one batch of points counted directly, for F_q (k = 1) and
+// F_{q^2} (k = 2), instead of flagging rows lane by lane: z(b, c) += 1 for every
+// x of the batch and every b with y_b(x) = u(x) + b x in F_q, c = -y_b(x).
+//   x in F_q: u(x) is in F_q too (the c_i are), so every b counts, with
+//     c = -(u + b x);
+//   x in F_{q^2} \ F_q: with u = u0 + u1 alpha, x = x0 + x1 alpha (x1 != 0),
+//     u + b x lies in F_q for exactly one b, b = -u1 / x1 = (-u1) A, and then
+//     c = -(u0 + b x0) = (-u0) + (-u1) B with A = 1/x1, B = -x0/x1.
+// KF = 1: all points are in F_q, whose digits come from zdig (zdig[l] = -alpha^l).
+// KF = 2: coordinate table crd[l] = -y0 | -y1 << 8 | A << 16 | B << 24 (A = 0,
+// B = -y0 for elements of F_q, the points alpha^j with j = 0 mod (q + 1));
+// jq walks those multiples of q + 1 across batches.
+// Us holds log u(x) (>= L for u = 0) of the batch's nb points from j0.
+template <int KF>
+__device__ __forceinline__ void fan2_zero_digits(const uint32_t *Us, uint32_t j0, uint32_t nb, uint32_t L,
+                                                 uint32_t q, int lane, uint32_t uA, uint32_t uB,
+                                                 const uint8_t *fq, const uint8_t *zdig, const uint32_t *crd,
+                                                 uint32_t *acc32, uint32_t &jq)
+{
+    const uint32_t qq = q * q;
+    const uint8_t *mulT = fq, *addT = fq + 2 * qq + q;
+    if constexpr (KF == 1) {
+        // -(u + b x) = (-u) + b (-x)
+        for (uint32_t i = 0; i < nb; ++i) {
+            const uint32_t lu = Us[i];
+            const uint32_t nu = lu < L ? zdig[lu] : 0u, nx = zdig[j0 + i];
+            if ((uint32_t)lane < q) zinc(acc32, q, (uint32_t)lane, addT[nu * q + mulT[(uint32_t)lane * q + nx]]);
+        }
+    } else {
+    // the lane's two points of the batch (x = j0 + lane + 32 h), both loads first
+    const uint32_t xA = j0 + (uint32_t)lane, xB = xA + 32u;
+    const bool vA = xA < j0 + nb, vB = xB < j0 + nb;
+    const uint32_t tA = crd[vA ? xA : 0u], tB = crd[vB ? xB : 0u];
+    uint32_t cA = crd[uA < L ? uA : 0u], cB = crd[uB < L ? uB : 0u];
+    cA = uA < L ? cA : 0u;
+    cB = uB < L ? cB : 0u;
+    if (vA && (tA & 0xFF0000u))
+        zinc(acc32, q, mulT[((cA >> 8) & 0xFFu) * q + ((tA >> 16) & 0xFFu)],
+             addT[(cA & 0xFFu) * q + mulT[((cA >> 8) & 0xFFu) * q + (tA >> 24)]]);
+    if (vB && (tB & 0xFF0000u))
+        zinc(acc32, q, mulT[((cB >> 8) & 0xFFu) * q + ((tB >> 16) & 0xFFu)],
+             addT[(cB & 0xFFu) * q + mulT[((cB >> 8) & 0xFFu) * q + (tB >> 24)]]);
+    for (; jq < j0 + nb; jq += q + 1) {   // x in F_q: u = u0, c = -u0 + b (-x0)
+        const uint32_t lu = Us[jq - j0];
+        const uint32_t n0 = lu < L ? (crd[lu] & 0xFFu) : 0u, nx = crd[jq] >> 24;
+        if ((uint32_t)lane < q) zinc(acc32, q, (uint32_t)lane, addT[n0 * q + mulT[(uint32_t)lane * q + nx]]);
+    }
+    }
+}
+
 // One block of 8 consecutive points x = alpha^(j0 + i) for lane (b, s), with
 // lb = log(b x) of the first point reduced mod L (later points lb + v, not
 // reduced).  Phases over the 8 points so that their lookups overlap: staged
@@ -91,8 +149,9 @@ __device__ __forceinline__ void drain_queue(const uint16_t *rq, uint32_t qn, int
 // fan-out row of y_b.  Row bit c is [chi(y_b + c) = -1]; the top bit flags
 // y_b in F_q (y_b = 0 included), whose zero digit goes to the lane's queue.
 // The row's top bit is counted too, in a position no member reads.
-// GEN: points outside okm are dropped, and u may be 0.
-template <bool GEN, class Tab>
+// GEN: points outside okm are dropped, and u may be 0.  QUEUE: queue the
+// flagged points (fields whose zero digits are not counted directly).
+template <bool GEN, bool QUEUE, class Tab>
 __device__ __forceinline__ void fan2_block(const Tab T, const uint32_t *__restrict__ rows, const uint32_t *Us,
                                            uint32_t L, uint32_t lb, bool b0, uint32_t okm, uint16_t *rq,
                                            uint32_t &qn, uint32_t (&a)[8])
@@ -119,7 +178,7 @@ __device__ __forceinline__ void fan2_block(const Tab T, const uint32_t *__restri
 #pragma unroll
     for (int v = 0; v < 8; ++v) {
         if (GEN && !((okm >> v) & 1u)) a[v] = 0u;
-        if ((int)a[v] < 0) {   // flagged: y in F_q (rare for k >= 3)
+        if (QUEUE && (int)a[v] < 0) {   // flagged: y in F_q (rare for k >= 3)
             rq[qn] = (uint16_t)ly[v];
             qn += 32;
         }
@@ -129,11 +188,15 @@ __device__ __forceinline__ void fan2_block(const Tab T, const uint32_t *__restri
 // points of one field for the whole group (all q^2 members), lane role (b, s)
 // The chain constants (lam_i and the h chain) come from the warp's shared
 // parameters at every batch: the main loop keeps no registers for them.
-template <int D, bool TRIPLE, bool PAD>
+// KF = 0: zero digits through the lanes' queues; KF = 1, 2: counted directly
+// per batch (fan2_zero_digits).
+template <int D, bool TRIPLE, bool PAD, int KF>
 __device__ __forceinline__ void group2_field(const KJob &J, int k, const uint8_t *smem, const HChain<D> *gH,
-                                             const uint32_t *glam, uint32_t nz, uint32_t *Us, uint16_t *acc_row,
-                                             uint16_t *rq, int lane, bool role, uint32_t b, uint32_t s, uint32_t S)
+                                             const uint32_t *glam, uint32_t nz, uint32_t *Us, uint16_t *acc,
+                                             uint16_t *acc_row, uint16_t *rq, int lane, bool role, uint32_t b,
+                                             uint32_t s, uint32_t S)
 {
+    constexpr bool QUEUE = KF == 0;
     const TabP<PAD> T{reinterpret_cast<const uint16_t *>(smem) + J.tab_off[k]};
     const uint32_t L = J.L[k];
     const uint32_t bar = J.barrett[k];
@@ -147,7 +210,8 @@ __device__ __forceinline__ void group2_field(const KJob &J, int k, const uint8_t
     uint32_t P[kFan2Planes];
 #pragma unroll
     for (int p = 0; p < kFan2Planes; ++p) P[p] = 0;
-    uint32_t nblk = 0, qn = (uint32_t)lane;
+    uint32_t nblk = 0, qn = (uint32_t)lane, jq = 0;
+    const uint32_t *crd = reinterpret_cast<const uint32_t *>(smem + J.coord_off);
     for (uint32_t j0 = 0; j0 < L; j0 += 64) {
         // log u(x) for the batch, two points per lane, staged for all lanes
         const uint32_t xA = j0 + lane, xB = j0 + 32 + lane;
@@ -164,19 +228,24 @@ __device__ __forceinline__ void group2_field(const KJob &J, int k, const uint8_t
         const bool uzero = __any_sync(0xFFFFFFFFu, uA >= L || uB >= L);
         __syncwarp();
         const uint32_t nb = min(64u, L - j0);   // points in this batch
+        if (!QUEUE) {   // atomics here, plain row updates (flushes) after the barrier
+            fan2_zero_digits<KF == 0 ? 1 : KF>(Us, j0, nb, L, J.q, lane, uA, uB, smem + J.fq_off, zdig, crd,
+                                               reinterpret_cast<uint32_t *>(acc), jq);
+            __syncwarp();
+        }
         if (pow2S && nb == 64 && !uzero) {
             const uint32_t per = 64 / S, i0 = s * per;
             uint32_t lb = addmod(lam_b, j0 + i0, L);
             for (uint32_t t0 = 0; t0 < per; t0 += 8) {
                 uint32_t a[8];
-                fan2_block<false>(T, rows, Us + i0 + t0, L, lb, b0, 0u, rq, qn, a);
+                fan2_block<false, QUEUE>(T, rows, Us + i0 + t0, L, lb, b0, 0u, rq, qn, a);
                 lb = addmod(lb, 8u % L, L);
                 add8_p10(P, a);
                 if (++nblk == kFan2FlushBlocks) {
                     flush_planes(P, acc_row, J.q, true);
                     nblk = 0;
                 }
-                if (__any_sync(0xFFFFFFFFu, qn >= 32 * (kFan2Queue - 8 + 1))) {   // more than 8 entries
+                if (QUEUE && __any_sync(0xFFFFFFFFu, qn >= 32 * (kFan2Queue - 8 + 1))) {   // more than 8 entries
                     drain_queue(rq, qn, lane, zdig, zdiv, L, acc_row);
                     qn = (uint32_t)lane;
                 }
@@ -190,14 +259,14 @@ __device__ __forceinline__ void group2_field(const KJob &J, int k, const uint8_t
                 const int nv = role ? min(8, max(0, (int)nb - (int)(i0 + t0))) : 0;
                 const uint32_t okm = (1u << nv) - 1u;
                 uint32_t a[8];
-                fan2_block<true>(T, rows, Us + i0 + t0, L, lb, b0, okm, rq, qn, a);
+                fan2_block<true, QUEUE>(T, rows, Us + i0 + t0, L, lb, b0, okm, rq, qn, a);
                 lb = addmod(lb, 8u % L, L);
                 add8_p10(P, a);
                 if (++nblk == kFan2FlushBlocks) {
                     flush_planes(P, acc_row, J.q, true);
                     nblk = 0;
                 }
-                if (__any_sync(0xFFFFFFFFu, qn >= 32 * (kFan2Queue - 8 + 1))) {   // more than 8 entries
+                if (QUEUE && __any_sync(0xFFFFFFFFu, qn >= 32 * (kFan2Queue - 8 + 1))) {   // more than 8 entries
                     drain_queue(rq, qn, lane, zdig, zdiv, L, acc_row);
                     qn = (uint32_t)lane;
                 }
@@ -206,7 +275,23 @@ __device__ __forceinline__ void group2_field(const KJob &J, int k, const uint8_t
         __syncwarp();   // U is rewritten by the next batch
     }
     flush_planes(P, acc_row, J.q, true);
-    drain_queue(rq, qn, lane, zdig, zdiv, L, acc_row);
+    if (QUEUE) drain_queue(rq, qn, lane, zdig, zdiv, L, acc_row);
+}
+
+// group2_field for the field's Zech layout (tripled or doubled, padded or not)
+template <int D, int KF>
+__device__ __forceinline__ void group2_field_tabs(const KJob &J, int k, bool tri, const uint8_t *smem,
+                                                  const HChain<D> *gH, const uint32_t *glam, uint32_t nz,
+                                                  uint32_t *Us, uint16_t *acc, uint16_t *acc_row, uint16_t *rq,
+                                                  int lane, bool role, uint32_t b, uint32_t s, uint32_t S)
+{
+    if (J.tab_pad[k]) {
+        if (tri) group2_field<D, true, true, KF>(J, k, smem, gH, glam, nz, Us, acc, acc_row, rq, lane, role, b, s, S);
+        else group2_field<D, false, true, KF>(J, k, smem, gH, glam, nz, Us, acc, acc_row, rq, lane, role, b, s, S);
+    } else {
+        if (tri) group2_field<D, true, false, KF>(J, k, smem, gH, glam, nz, Us, acc, acc_row, rq, lane, role, b, s, S);
+        else group2_field<D, false, false, KF>(J, k, smem, gH, glam, nz, Us, acc, acc_row, rq, lane, role, b, s, S);
+    }
 }
 
 // Square-freeness of the q members f_c = g_b + c (c in F_q) that share
@@ -338,7 +423,6 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
     unsigned long long *keys =
         J.wkeys + ((uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * J.wkeys_stride;
 
-    const uint16_t *s16 = reinterpret_cast<const uint16_t *>(smem);
     const uint32_t *s32 = reinterpret_cast<const uint32_t *>(smem);
     const uint8_t *mulT = smem + J.fq_off;
     const uint8_t *subT = mulT + qq;
@@ -421,12 +505,18 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
         for (uint32_t m = lane; m < acc_words; m += 32) reinterpret_cast<uint32_t *>(acc)[m] = 0;
         __syncwarp();
         const bool tri = J.tab_kind[k] == kTabTripleSmem;
-        if (J.tab_pad[k]) {
-            if (tri) group2_field<D, true, true>(J, k, smem, gH, glam, nz, Us, acc_row, rq, lane, role, b, s, S);
-            else group2_field<D, false, true>(J, k, smem, gH, glam, nz, Us, acc_row, rq, lane, role, b, s, S);
+        // zero digits: counted directly in F_q and F_{q^2} (with its coordinates)
+        // when g <= 2; queued for g >= 3, whose time is in F_{q^3} and up (one
+        // copy of the field loop for every field keeps the instruction cache warm)
+        // (degrees 2g+1, 2g+2 >= 7 are g >= 3: no direct copies compiled)
+        const int kf = J.g > 2 ? 0 : (k == 0 ? 1 : (J.coord_off ? 2 : 0));
+        if constexpr (D <= 6) {
+            if (kf == 1) group2_field_tabs<D, 1>(J, k, tri, smem, gH, glam, nz, Us, acc, acc_row, rq, lane, role, b, s, S);
+            else if (kf == 2) group2_field_tabs<D, 2>(J, k, tri, smem, gH, glam, nz, Us, acc, acc_row, rq, lane, role, b, s, S);
+            else group2_field_tabs<D, 0>(J, k, tri, smem, gH, glam, nz, Us, acc, acc_row, rq, lane, role, b, s, S);
         } else {
-            if (tri) group2_field<D, true, false>(J, k, smem, gH, glam, nz, Us, acc_row, rq, lane, role, b, s, S);
-            else group2_field<D, false, false>(J, k, smem, gH, glam, nz, Us, acc_row, rq, lane, role, b, s, S);
+            (void)kf;
+            group2_field_tabs<D, 0>(J, k, tri, smem, gH, glam, nz, Us, acc, acc_row, rq, lane, role, b, s, S);
         }
         __syncwarp();
         // sum_x chi(f_{b,c}(x)) = (L - sum_s acc[s q + b][c]) + chi(c)   (x = 0: y = 0)

@@ -66,6 +66,10 @@ struct Tables {
     uint8_t *d_fq_mul = nullptr;
     uint8_t *d_fq_sub = nullptr;
     uint8_t *d_fq_inv = nullptr;
+    // coordinates of F_{q^2} over F_q in the basis {1, alpha} (k = 2, q <= 31),
+    // for alpha^l = e_y0 + e_y1 alpha: bits 0-7 -y0, bits 8-15 -y1; bits 16-23
+    // 1/y1 and bits 24-31 -y0/y1 when y1 != 0, else 0 and -y0 (digits)
+    uint32_t *d_coord2 = nullptr;   // [L]
 };
 
 // where a count kernel reads the Zech table of one field
@@ -122,6 +126,8 @@ struct KJob {
     uint32_t wkeys_stride, pad3;      //   slot blockIdx.x * warps + warp, stride q^2
     const uint8_t *fq_mul, *fq_sub, *fq_inv;   // digit arithmetic of F_q (fan-out jobs)
     uint32_t fq_off;                  // byte offset of mul | sub | inv | add in smem
+    const uint32_t *coord2;           // method 2, g = 2: coordinates of F_{q^2} (Tables::d_coord2)
+    uint32_t coord_off, pad4;         // byte offset of coord2 in smem; 0: not staged
     // outputs
     unsigned long long *hkeys;        // [hmask+1]
     unsigned long long *hcounts;      // [hmask+1]

@@ -131,6 +131,7 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit, bool no_triple)
         uint64_t b = 0;
         for (uint32_t k = 0; k < j.g; ++k) b += ((row_bytes(k) + 15) / 16) * 16 + ((j.q + 15) / 16) * 16;
         b += ((3ull * j.q * j.q + j.q + 15) / 16) * 16;
+        if (j.method == 2 && j.g == 2 && j.coord2) b += ((4ull * j.L[1] + 15) / 16) * 16;
         if (j.method == 2) b += 16 + (uint64_t)kFan2WarpsHost * fan2_warp_bytes(j.q, false);   // smallest block
         return b;
     };
@@ -188,6 +189,11 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit, bool no_triple)
     }
     j.fq_off = bytes;
     if (j.method != 0) bytes += ((3 * j.q * j.q + j.q + 15) / 16) * 16;   // mul | sub | inv | add
+    j.coord_off = 0;
+    if (j.method == 2 && j.g == 2 && j.coord2) {   // coordinates of F_{q^2} (direct zero digits, g = 2)
+        j.coord_off = bytes;
+        bytes += ((4 * j.L[1] + 15) / 16) * 16;
+    }
     j.warp_off = 0;
     j.warp_bytes = 0;
     j.dense_off = 0;
@@ -286,6 +292,7 @@ int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n, uint32_t flags, co
             kj.fq_inv = t->d_fq_inv;
         }
         kj.zdig[k - 1] = t->d_zdig;
+        if (k == 2) kj.coord2 = t->d_coord2;
         // ceil(2^32 / s) recovers l / s exactly for multiples l of s = L/(q-1) < 2^32;
         // s = 1 (k = 1) is encoded as 0
         const uint32_t sdiv = t->L / (jb.q - 1);

@@ -353,6 +353,39 @@ __global__ void k_fq_digit_tables(uint32_t q, uint32_t L, const uint32_t *__rest
     }
 }
 
+// coordinates of F_{q^2} over F_q in the basis {1, alpha}, for alpha^l = e_y0 + e_y1 alpha:
+// coord[l] = -y0 | -y1 << 8 | A << 16 | B << 24 with A = 1/y1, B = -y0/y1 when
+// y1 != 0, A = 0, B = -y0 when y1 = 0 (digits).  alpha generates F_{q^2}^x, so it
+// is not in F_q and every nonzero (y0, y1) names one log:
+// e_y0 + e_y1 alpha = e_y0 (1 + alpha^(1 + log e_y1 - log e_y0)) (eq. 2.1).
+// Digit arithmetic goes through logs: F_q^x = <alpha^s>, s = L/(q-1).  One block.
+__global__ void k_coord2(uint32_t q, uint32_t L, const uint32_t *__restrict__ zech,
+                         const uint32_t *__restrict__ coef_log, uint32_t *coord)
+{
+    __shared__ uint8_t dig[64];   // dig[l / s]: the digit with log l
+    const uint32_t s = L / (q - 1), h = L / 2;   // alpha^(L/2) = -1
+    for (uint32_t c = threadIdx.x; c < q; c += blockDim.x)
+        if (c) dig[coef_log[c] / s] = (uint8_t)c;
+    __syncthreads();
+    auto digit = [&](uint32_t l) -> uint32_t { return dig[(l % L) / s]; };
+    for (uint32_t i = threadIdx.x; i < q * q; i += blockDim.x) {
+        const uint32_t y0 = i % q, y1 = i / q;
+        if (i == 0) continue;
+        const uint32_t l0 = coef_log[y0], l1 = coef_log[y1];
+        uint32_t l;
+        if (y1 == 0) l = l0;
+        else if (y0 == 0) l = (l1 + 1) % L;
+        else l = (l0 + zech[(l1 + L - l0 + 1) % L]) % L;   // the Zech value is not L: alpha is not in F_q
+        const uint32_t n0 = y0 ? digit(l0 + h) : 0u, n1 = y1 ? digit(l1 + h) : 0u;
+        uint32_t A = 0, B = n0;
+        if (y1) {
+            A = digit(L - l1);
+            B = y0 ? digit(l0 + h + L - l1) : 0u;
+        }
+        coord[l] = n0 | (n1 << 8) | (A << 16) | (B << 24);
+    }
+}
+
 struct ElemArgs {
     uint32_t p, e, q, n, L;
     uint32_t mq[kMaxE + 1];
@@ -425,6 +458,7 @@ void tables_destroy(Tables *t)
     cudaFree(t->d_fq_mul);
     cudaFree(t->d_fq_sub);
     cudaFree(t->d_fq_inv);
+    cudaFree(t->d_coord2);
     if (t->device >= 0 && t->device != cur && cur >= 0) cudaSetDevice(cur);
     delete t;
 }
@@ -549,6 +583,14 @@ int tables_build(uint32_t q, uint32_t k, Tables **out)
             }
             k_fq_digit_tables<<<(q * q + 255) / 256, 256, L>>>(q, L, t->d_zech, t->d_coef_log, t->d_fq_mul,
                                                                t->d_fq_sub, t->d_fq_inv);
+        }
+        if (k == 2 && q <= 31) {
+            if (cudaMalloc(&t->d_coord2, sizeof(uint32_t) * L) != cudaSuccess) {
+                cudaFree(d_best);
+                return fail(set_error(HWC_ERR_NOMEM, "cudaMalloc of F_%u coordinates failed", t->Q));
+            }
+            cudaMemset(t->d_coord2, 0, sizeof(uint32_t) * L);   // every entry is written; zero keeps digits in range
+            k_coord2<<<1, 256>>>(q, L, t->d_zech, t->d_coef_log, t->d_coord2);
         }
     }
     cudaError_t ce = cudaDeviceSynchronize();
