@@ -246,9 +246,10 @@ int hwc_serve_close(hwc_server_t *s);
 /* Counting without device allocation                                  */
 
 /* Histogram of one job for callers that cannot allocate device memory when
- * they count (for example while a stream is being captured into a CUDA
- * graph, or in a process that reserves device memory up front and forbids
- * further cudaMalloc).  The paper has no counterpart; it is the count of
+ * they count: for example a process that reserves the device memory up front
+ * and forbids further cudaMalloc, or a host thread that must not call
+ * cudaMalloc because it synchronises the device.  The paper has no
+ * counterpart; it is the count of
  * hwc_count through the per-member kernel with its working memory in a fixed
  * device array instead of allocations.
  *  - Calls no cudaMalloc, cudaFree or other allocating routine.  The hash,

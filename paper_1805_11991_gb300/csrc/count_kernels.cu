@@ -190,11 +190,10 @@ int launch_compact(const KJob *d_jobs, uint32_t n_jobs, cudaStream_t s)
 // ---------------------------------------------------------------------
 // Histogram without device allocation (hwc_count_noalloc).
 //
-// Some callers cannot call cudaMalloc when they count: code that runs while a
-// stream is being captured into a CUDA graph (allocation would break the
-// capture), processes that reserve all device memory up front and hand out
-// fixed pools, or host applications whose plug-in rules forbid device
-// allocation.  This entry point keeps all of its working memory in one
+// Some callers cannot call cudaMalloc when they count: processes that reserve
+// all device memory up front and hand out fixed pools, threads that must not
+// block on the device-wide synchronisation cudaMalloc implies, or host
+// applications whose plug-in rules forbid device allocation.  This entry point keeps all of its working memory in one
 // file-scope device array of fixed size: the histogram hash (keys and
 // counts), the member statistics and the entry counter.  The job descriptor
 // travels as a kernel parameter, the field tables are the caller's handles

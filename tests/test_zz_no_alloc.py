@@ -1,8 +1,9 @@
 """The allocation-free histogram entry point (hwc_count_noalloc) against the
 regular one (hwc_count): the same histogram, exactly, on calls in a row.
 
-Some callers cannot allocate device memory when they count (inside a stream
-capture, or in processes whose device memory is reserved up front); this
+Some callers cannot allocate device memory when they count (processes whose
+device memory is reserved up front, or threads that must not call the
+synchronising cudaMalloc); this
 entry point keeps its working memory in a fixed device array and writes into
 buffers the caller owns.  This file runs last so that a failure here leaves
 every other test already run."""
