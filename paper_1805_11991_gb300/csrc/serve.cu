@@ -2,9 +2,11 @@
 //
 // A server thread owns a CUDA stream and runs the device in steps.  Each step
 // is one launch of the persistent count kernel over a slice of every active
-// request (a fair share of tiles each), so requests of very different sizes
-// progress together and a request that arrives while others run joins at the
-// next step boundary once a slot and enough device memory are free.  Field
+// request (an equal share of point evaluations each, about kStepMs of device
+// time in all at the rate measured on earlier steps), so requests of very
+// different sizes progress together and a request that arrives while others
+// run joins at the next step boundary once a slot and enough device memory
+// are free.  Field
 // tables stay resident in the process-wide table cache.  Each request owns its
 // histogram hash; slices of one request add into it across steps, and when
 // its last slice is done the hash is compacted and copied out.  Results do not
@@ -65,9 +67,25 @@ struct hwc_server {
     unsigned long long *d_wkeys = nullptr;   // two-level kernel: member keys per resident warp
     uint64_t wkeys_slots = 0;
     uint64_t steps = 0;
+    double evals_per_ms = 0;   // device rate of earlier steps (running mean); 0 before the first
 };
 
 namespace {
+
+// device time a step aims at, and the rate assumed before one was measured
+constexpr double kStepMs = 4.0;
+constexpr double kFirstEvalsPerMs = 1e9;
+
+// nominal point evaluations of one tile of a job: members per tile (q^2
+// for the two-level fan-out, q for the c_0 fan-out, 32 per member tile)
+// times sum_k q^k
+double tile_evals(const KJob &kj)
+{
+    const double members = kj.method == 2 ? (double)kj.q * kj.q : (kj.method == 1 ? (double)kj.q : (double)kTileMembers);
+    double pts = 0;
+    for (uint32_t k = 0; k < kj.g; ++k) pts += kj.Q[k];
+    return members * pts;
+}
 
 void free_request_device(Request *r)
 {
@@ -201,6 +219,8 @@ void server_loop(hwc_server *s)
                          [&](const Request *x, const Request *y) { return skey(x) < skey(y); });
         const uint32_t n = (uint32_t)step.size();
         std::vector<uint64_t> took(n, 0);
+        // equal point evaluations per request, the step about kStepMs in all
+        const double req_evals = (s->evals_per_ms > 0 ? s->evals_per_ms : kFirstEvalsPerMs) * kStepMs / n;
         int rc = HWC_OK;
         uint32_t item_off = 0, ngroups = 0;
         struct StepGroup {
@@ -229,8 +249,10 @@ void server_loop(hwc_server *s)
                 rc = shape_for(s, G.D, G.method, G.words, smem, &G.sh);
             }
             if (rc) break;
-            // per launch: about 8 work items per CTA (the tail of a launch weighs
-            // little), shared evenly by the group's requests
+            // per request: its share of the step's point evaluations (req_evals),
+            // and at least its share of about 8 work items per CTA of the launch
+            // (the tail of a launch then weighs little); with step_items set by
+            // the caller, exactly its share of step_items items per launch
             uint64_t budget = s->cfg.step_items ? s->cfg.step_items : (uint64_t)G.sh.grid * 8;
             budget *= (uint64_t)G.sh.item_tiles;
             const uint64_t share = std::max<uint64_t>(G.sh.item_tiles, budget / (e - i));
@@ -239,7 +261,10 @@ void server_loop(hwc_server *s)
                 Request *q = step[r];
                 KJob sl = q->kj;
                 const uint64_t left = q->kj.n_tiles - q->next_tile;
-                const uint64_t t = std::min(left, share);
+                uint64_t want = share;
+                if (!s->cfg.step_items)
+                    want = std::max<uint64_t>(want, (uint64_t)(req_evals / tile_evals(q->kj)) + 1);
+                const uint64_t t = std::min(left, want);
                 took[r] = t;
                 if (q->kj.method != 0) {
                     // fan-out tiles are groups; the member range stays the request's
@@ -263,6 +288,7 @@ void server_loop(hwc_server *s)
             i = e;
         }
         cudaError_t ce = cudaSuccess;
+        const Clock::time_point t_step = Clock::now();
         if (rc == HWC_OK) {
             ce = cudaMemcpyAsync(s->d_jobs, s->h_jobs, n * sizeof(KJob), cudaMemcpyHostToDevice, s->stream);
             if (ce == cudaSuccess)
@@ -280,6 +306,13 @@ void server_loop(hwc_server *s)
         if (rc == HWC_OK) {
             ce = cudaStreamSynchronize(s->stream);
             if (ce != cudaSuccess) rc = set_error(HWC_ERR_CUDA, "step: %s", cudaGetErrorString(ce));
+        }
+        if (rc == HWC_OK) {   // the step's rate updates the running mean
+            const double ms = std::chrono::duration<double, std::milli>(Clock::now() - t_step).count();
+            double ev = 0;
+            for (uint32_t i = 0; i < n; ++i) ev += (double)took[i] * tile_evals(step[i]->kj);
+            if (ms > 0 && ev > 0)
+                s->evals_per_ms = s->evals_per_ms > 0 ? 0.5 * s->evals_per_ms + 0.5 * (ev / ms) : ev / ms;
         }
         ++s->steps;
 
