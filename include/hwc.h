@@ -6,7 +6,8 @@
  * returns the exact histogram of the tuples (#C_f(F_q), ..., #C_f(F_{q^g}))
  * over the square-free members f.  This is the inner part of Algorithm 1 of
  * Raum, "Hyperelliptic curves over small finite fields and GPU accelerators"
- * (arXiv:1805.11991): lines 3-17 and the increment of line 21 with weight 1.
+ * (arXiv:1805.11991): from the choice of f through the point counts, and the
+ * histogram increment with weight 1.
  *
  * Conventions shared by every entry point
  *  - Return value: HWC_OK (0) or a negative HWC_ERR_* code.  Nothing throws
@@ -48,7 +49,7 @@ extern "C" {
 #define HWC_MAX_Q 262144u      /* largest field size F_{q^k} accepted       */
 #define HWC_MAX_G 4u
 
-/* Families of f (Sec. 1.1, Algorithm 1 line 3).  Member idx decodes to
+/* Families of f (Sec. 1.1, Algorithm 1).  Member idx decodes to
  * c_0..c_d by base-q digits of idx, little endian:
  *  HWC_FAM_ALL_DEG       exact degree d, any lead: c_i = digit i of
  *                        (idx mod q^d) for i < d, c_d = 1 + floor(idx / q^d);
@@ -139,8 +140,8 @@ int hwc_family_size(uint32_t q, const hwc_family_t *fam, uint64_t *n);
                                      two-level (c_1, c_0) kernel applies */
 
 /* Histogram of (#C(F_q), ..., #C(F_{q^g})) over the square-free members
- * [first, first+count) of the family (Algorithm 1 lines 3-17 and 21, every
- * weight 1).  Synchronous on `stream`; *out receives a library-owned
+ * [first, first+count) of the family (Algorithm 1: point counts and the
+ * histogram increment, every weight 1).  Synchronous on `stream`; *out receives a library-owned
  * histogram.  Errors: HWC_ERR_ARG, HWC_ERR_RANGE, HWC_ERR_TOO_LARGE,
  * HWC_ERR_NOMEM, HWC_ERR_CUDA. */
 int hwc_count(uint32_t g, uint32_t q, const hwc_family_t *fam, uint64_t first,

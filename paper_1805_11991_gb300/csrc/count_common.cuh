@@ -53,7 +53,7 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t j)
 }
 
 // ---------------------------------------------------------------------
-// member decoding (Algorithm 1 line 3; family definitions in hwc.h)
+// member decoding (the choice of f in Algorithm 1; family definitions in hwc.h)
 
 template <int D>
 __device__ __forceinline__ void decode_member(const KJob &J, uint64_t m, uint32_t (&c)[D + 1])

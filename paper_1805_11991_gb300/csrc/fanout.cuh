@@ -15,8 +15,8 @@
 // the number of x with y = -c != 0 (rare: y in F_q^x, flagged in the row):
 //     sum_x chi(f_c(x)) = n_0 chi(c) + (Q - n_0) - 2 cnt_c - z_c,
 //     #C_k(f_c) = Q + sum_x chi(f_c(x)) + 1 + chi(f(inf))          (Sec. 1.1).
-// Members are counted exactly as in Algorithm 1 lines 7-14; only the work
-// shared by the q members of a group is done once.
+// Members are counted exactly as Algorithm 1's evaluation loop counts them;
+// only the work shared by the q members of a group is done once.
 #pragma once
 #include "count_common.cuh"
 

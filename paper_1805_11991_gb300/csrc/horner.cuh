@@ -2,18 +2,19 @@
 // degree in horner_a.cu (d = 3..6) and horner_b.cu (d = 7..10).
 //
 // One warp handles a tile of 32 consecutive members of a family:
-//   1. each lane decodes one member index into coefficient digits (Algorithm 1
-//      line 3) and tests it for square-freeness by Euclid's algorithm on
-//      gcd(f, f') in Zech arithmetic over F_q;
+//   1. each lane decodes one member index into coefficient digits (the choice
+//      of f in Algorithm 1) and tests it for square-freeness by Euclid's
+//      algorithm on gcd(f, f') in Zech arithmetic over F_q;
 //   2. for every square-free member of the tile (uniform loop) and every
-//      k = 1..g the 32 lanes sweep x = alpha^j over F_Q^x (lines 6-14), two
+//      k = 1..g the 32 lanes sweep x = alpha^j over F_Q^x (the evaluation
+//      loop of Algorithm 1), two
 //      x per lane per step, evaluating f by Horner's rule in the log domain
 //      with one Zech lookup per nonzero coefficient (eq. 2.1, 3.1-3.2), and
 //      sum chi(f(x)) = (-1)^log (the parity of the log, L being even);
 //   3. #C_k = Q + sum_x chi(f(x)) + 1 + chi(f(inf)) (Sec. 1.1), i.e.
 //      r^0 + 2 r^sq + 1 + chi(f(inf)); the lanes' tuples are aggregated
 //      within the warp (match.any) and added into an open-addressing hash
-//      in global memory (line 21, weight 1).
+//      in global memory (the histogram increment of Algorithm 1, weight 1).
 //
 // The Horner chain is kept in "Zech index" form.  With lambda_i = log c_i and
 // the nonzero coefficients below the lead at i_1 > i_2 > ..., the partial
