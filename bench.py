@@ -92,12 +92,13 @@ def table_reads(spec: JobSpec, n_squarefree: int, method: int) -> float:
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline leg and --impl reference)
 
-def oracle_rate(jobs, seconds: float, offset_frac: float = 0.0):
+def oracle_rate(jobs, seconds: float, offset_frac: float = 0.0, threads: int | None = None):
     """Time the oracle on a bounded sample: the same number of members from
     each job, starting at offset_frac of the family; returns
-    (evals/s of square-free members, members/s, threads, sample text)."""
+    (evals/s of square-free members, members/s, threads, sample text).
+    threads: OpenMP threads (all host cores by default)."""
     import oracle
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     # calibrate on a tiny slice
     probe = 64 * threads
     t0 = time.perf_counter()
@@ -116,7 +117,7 @@ def oracle_rate(jobs, seconds: float, offset_frac: float = 0.0):
         evals += int(sqf.sum()) * evals_per_member(s)
         members += n
     dt = time.perf_counter() - t0
-    sample = f"{per} consecutive members of each of the {len(jobs)} jobs"
+    sample = f"{members} members: up to {per} consecutive members of each of the {len(jobs)} jobs"
     return evals / dt, members / dt, threads, sample
 
 
@@ -139,6 +140,7 @@ def run_reference(args):
         rates.append(r)
         curves.append(c)
     value = statistics.mean(rates)
+    r1, _, _, sample1 = oracle_rate(jobs, 4.0, offset_frac=0.5, threads=1)   # the paper's CPU column is 1 core
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -147,7 +149,8 @@ def run_reference(args):
         "config": {"workload": args.config, "jobs": [j.__dict__ for j in jobs]},
         "curves_per_s": statistics.mean(curves),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"each step: {sample} (a different slice per step)"},
+                         "sample": f"each step: {sample} (a different slice per step)",
+                         "value_1core": r1, "sample_1core": sample1},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -414,8 +417,9 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, c, threads, sample = oracle_rate(jobs, args.cpu_seconds)
+        r1, _, _, sample1 = oracle_rate(jobs, 4.0, offset_frac=0.5, threads=1)   # the paper's CPU column is 1 core
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle",
-                                "sample": sample, "curves_per_s": c}
+                                "sample": sample, "curves_per_s": c, "value_1core": r1, "sample_1core": sample1}
     if args.serve and rank == 0:
         line["served"] = serve_leg(hwc, jobs, results, value / world, args.serve_requests, args.serve_load)
     line["clocks"] = clk.summary()
