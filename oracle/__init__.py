@@ -11,6 +11,7 @@ r^sq and the points at infinity) with polynomial-basis field arithmetic
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -80,6 +81,10 @@ def _load():
         lib.orc_count_polys.restype = i32
         lib.orc_count_polys.argtypes = [i32, i32, i32, i32, u64, u64, u64, u64,
                                         i32, i32, i32, i32, P32, P8]
+        u32 = ctypes.c_uint32
+        P64 = ctypes.POINTER(ctypes.c_uint64)
+        lib.hwc_cpu_count.restype = i32
+        lib.hwc_cpu_count.argtypes = [u32, u32, u32, u32, u64, u64, u64, u64, i32, u64, P32, P64, P64, P64]
         _lib = lib
         return lib
 
@@ -183,3 +188,29 @@ def histogram(counts: np.ndarray, sqf: np.ndarray):
 def count_histogram(g: int, q: int, kind: int, degree: int, first: int, count: int, **kw):
     counts, sqf = count_polys(g, q, kind, degree, first, count, **kw)
     return histogram(counts, sqf)
+
+
+def cpu_count(g: int, q: int, kind: int, degree: int, first: int, count: int, *,
+              seed: int = 0, sample_count: int = 0, threads: int | None = None):
+    """hwc_cpu_count: the oracle's histogram in one call.  Returns (tuples
+    int32[n, g] sorted lexicographically, multiplicities uint64[n],
+    number of square-free members)."""
+    lib = _load()
+    if threads is None:
+        threads = os.cpu_count() or 1
+    n_e, n_sq = ctypes.c_uint64(), ctypes.c_uint64()
+    P64 = ctypes.POINTER(ctypes.c_uint64)
+    # distinct tuples: at most the members, and at most the Hasse-Weil box
+    # |q^k + 1 - #C_k| <= 2 g q^(k/2) of square-free members
+    box = 1
+    for k in range(1, g + 1):
+        box *= 2 * math.isqrt(4 * g * g * q ** k) + 1
+    cap = max(1, min(count, box))
+    counts = np.zeros((cap, g), np.int32)
+    mult = np.zeros(cap, np.uint64)
+    rc = lib.hwc_cpu_count(g, q, kind, degree, seed, sample_count, first, count, threads, cap,
+                           _p32(counts), mult.ctypes.data_as(P64), ctypes.byref(n_e), ctypes.byref(n_sq))
+    if rc != 0:
+        raise ValueError(f"hwc_cpu_count failed rc={rc}")
+    n = n_e.value
+    return counts[:n].copy(), mult[:n].copy(), n_sq.value

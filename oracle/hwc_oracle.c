@@ -537,3 +537,114 @@ int orc_count_polys(int g, int q, int kind, int d, uint64_t seed, uint64_t sampl
     for (int k = 1; k <= g; ++k) orc_field_free(F[k]);
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* the histogram                                                       */
+
+/* lexicographic order of #C tuples; the tuple width is set per call */
+static int g_cmp_width;
+
+static int cmp_tuple(const void *a, const void *b)
+{
+    const int32_t *x = (const int32_t *)a, *y = (const int32_t *)b;
+    for (int k = 0; k < g_cmp_width; ++k)
+        if (x[k] != y[k]) return x[k] < y[k] ? -1 : 1;
+    return 0;
+}
+
+/* hwc_cpu_count: the histogram of (#C(F_q), ..., #C(F_{q^g})) over the
+ * square-free members [first, first+count) of a family, computed by this
+ * oracle (the same job arguments as the GPU library's hwc_count, the family
+ * given as kind, degree, seed, sample_count; no stream).  Algorithm 1's
+ * histogram with weight 1 per member.
+ *   counts[max_entries * g]: distinct tuples, sorted lexicographically;
+ *   mult[max_entries]: their multiplicities;
+ *   *n_entries: number of distinct tuples; *n_squarefree: square-free members.
+ * Members are counted in slices of at most 2^20 (bounded memory); slice
+ * histograms are merged.  Returns 0; -1 bad argument, -2 range, -3 field or
+ * allocation failure, -4 more than max_entries tuples (*n_entries then holds
+ * the number needed).  Not thread-safe (one call at a time). */
+int hwc_cpu_count(uint32_t g, uint32_t q, uint32_t kind, uint32_t degree, uint64_t seed,
+                  uint64_t sample_count, uint64_t first, uint64_t count, int nthreads,
+                  uint64_t max_entries, int32_t *counts, uint64_t *mult, uint64_t *n_entries,
+                  uint64_t *n_squarefree)
+{
+    if (!n_entries || !n_squarefree || (max_entries && (!counts || !mult))) return -1;
+    if (g < 1 || g > ORC_MAXK) return -1;
+    const uint64_t slice = 1u << 20;
+    const int G = (int)g;
+    int32_t *pc = NULL, *tup = NULL, *acc = NULL, *nxt = NULL;
+    uint8_t *ps = NULL;
+    uint64_t *accm = NULL, *nxtm = NULL, *tm = NULL;
+    uint64_t nacc = 0, nsq = 0;
+    int rc = 0;
+    const uint64_t cap = count < slice ? (count ? count : 1) : slice;
+    pc = (int32_t *)malloc(sizeof(int32_t) * cap * G);
+    tup = (int32_t *)malloc(sizeof(int32_t) * cap * G);
+    tm = (uint64_t *)malloc(sizeof(uint64_t) * cap);
+    ps = (uint8_t *)malloc(cap);
+    if (!pc || !tup || !tm || !ps) { rc = -3; goto out; }
+    for (uint64_t s0 = 0; s0 < count || (count == 0 && s0 == 0); s0 += slice) {
+        const uint64_t n = count - s0 < slice ? count - s0 : slice;
+        rc = orc_count_polys(G, (int)q, (int)kind, (int)degree, seed, sample_count, first + s0, n, 1, 0, 0,
+                             nthreads, pc, ps);
+        if (rc) goto out;
+        if (count == 0) break;
+        /* this slice's square-free tuples, sorted and run-length encoded */
+        uint64_t m = 0;
+        for (uint64_t i = 0; i < n; ++i)
+            if (ps[i]) { memcpy(tup + m * G, pc + i * G, sizeof(int32_t) * G); ++m; }
+        nsq += m;
+        g_cmp_width = G;
+        qsort(tup, m, sizeof(int32_t) * G, cmp_tuple);
+        uint64_t u = 0;
+        for (uint64_t i = 0; i < m; ++i) {
+            if (u && cmp_tuple(tup + (u - 1) * G, tup + i * G) == 0) { ++tm[u - 1]; continue; }
+            memmove(tup + u * G, tup + i * G, sizeof(int32_t) * G);
+            tm[u++] = 1;
+        }
+        /* merge with the running histogram */
+        nxt = (int32_t *)malloc(sizeof(int32_t) * (nacc + u) * G + 1);
+        nxtm = (uint64_t *)malloc(sizeof(uint64_t) * (nacc + u) + 1);
+        if (!nxt || !nxtm) { rc = -3; goto out; }
+        uint64_t a = 0, b = 0, o = 0;
+        while (a < nacc || b < u) {
+            int c = a == nacc ? 1 : (b == u ? -1 : cmp_tuple(acc + a * G, tup + b * G));
+            if (c <= 0) {
+                memcpy(nxt + o * G, acc + a * G, sizeof(int32_t) * G);
+                nxtm[o] = accm[a] + (c == 0 ? tm[b] : 0);
+                ++a;
+                if (c == 0) ++b;
+            } else {
+                memcpy(nxt + o * G, tup + b * G, sizeof(int32_t) * G);
+                nxtm[o] = tm[b];
+                ++b;
+            }
+            ++o;
+        }
+        free(acc);
+        free(accm);
+        acc = nxt;
+        accm = nxtm;
+        nxt = NULL;
+        nxtm = NULL;
+        nacc = o;
+    }
+    *n_entries = nacc;
+    *n_squarefree = nsq;
+    if (nacc > max_entries) { rc = -4; goto out; }
+    if (nacc) {
+        memcpy(counts, acc, sizeof(int32_t) * nacc * G);
+        memcpy(mult, accm, sizeof(uint64_t) * nacc);
+    }
+out:
+    free(pc);
+    free(tup);
+    free(tm);
+    free(ps);
+    free(acc);
+    free(accm);
+    free(nxt);
+    free(nxtm);
+    return rc;
+}
