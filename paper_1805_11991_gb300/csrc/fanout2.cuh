@@ -17,7 +17,9 @@
 //     sum_x chi(f_{b,c}(x)) = n_0 chi(c) + (Q - n_0) - 2 cnt(b, c) - z(b, c),
 //     #C_k(f_{b,c}) = Q + sum_x chi(f_{b,c}(x)) + 1 + chi(f(inf))   (Sec. 1.1).
 // Per point and member this is 1/q Zech additions and one row bit; the chain
-// for u and every per-group cost are shared by q^2 members.
+// for u and every per-group cost are shared by q^2 members.  z(b, c) is
+// counted directly per point for g <= 2 (fan2_zero_digits: one b per point
+// outside F_q) and through the lanes' queues of flagged rows for g >= 3.
 #pragma once
 #include "fanout.cuh"
 
