@@ -1,16 +1,26 @@
 #!/usr/bin/env python
 """Benchmark: point evaluations per second of the GPU point count.
 
-Workload (one "step"): g=2, q=31 and q=27, the full monic degree-5 and
-degree-6 families with zero x^(d-1) coefficient (q^4 + q^5 members each),
-counts over F_q and F_{q^2}, exact histograms -- all four jobs in one
-persistent launch replayed from a CUDA graph (clear, count, compact).
+Workload (one "step", default --config config4, the largest workload that
+fits one GPU): g=3, q in {13, 17, 25, 27}, the full monic degree-7 families
+with zero x^6 coefficient (q^6 members each, 6.6e8 in all), counts over F_q,
+F_{q^2} and F_{q^3}, exact histograms -- all four jobs in one persistent
+launch replayed from a CUDA graph (clear, count, compact).
 
 value  = point evaluations of square-free members per second, device-timed
          (CUDA events on the launch stream, L2 flushed between steps);
 e2e    = the same through the public C ABI with host results (descriptor
          upload from pinned memory, launch, histogram copy-back and sort);
 plain  = the same jobs with one launch per job (no persistent queue, no graph).
+At one GPU the line also carries, each with its own device times:
+  config3 = the mixed-q workload (g=2, every odd prime power q < 64 plus
+            2^24 sampled members over F_293), batched against plain;
+  config2 = g=2, q = 31 and 27, batched;
+  served  = configuration 2 as Poisson-timed requests through the server
+            (p50/p99 latency, results against the batched histograms).
+Under torchrun (N > 1) every job's member range is split across the ranks
+(contiguous shards, no collective on the data path) and the shards'
+histograms are gathered and merged after the timed region.
 
 --impl reference times the CPU oracle (oracle/) on bounded samples of the
 same workload instead.
@@ -43,7 +53,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hwc", choices=["hwc", "reference"])
-    ap.add_argument("--config", default="config2", choices=sorted(CONFIGS))
+    ap.add_argument("--config", default="config4", choices=sorted(CONFIGS))
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the config3 / config2 / served extras of the one-GPU line")
+    ap.add_argument("--extra-steps", type=int, default=2,
+                    help="timed steps of the config3 extra (batched and plain each)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--serve", action="store_true",
@@ -70,9 +84,32 @@ def chain_reads(spec: JobSpec, lo: int) -> float:
     return free * (q - 1) / q
 
 
+def _mobius(n: int) -> int:
+    r, k, p = 1, n, 2
+    while p * p <= k:
+        if k % p == 0:
+            k //= p
+            if k % p == 0:
+                return 0
+            r = -r
+        p += 1
+    return -r if k > 1 else r
+
+
+def points_per_member(spec: JobSpec) -> int:
+    """Points x != 0 the kernels evaluate per member: every x in F_q^x, and one
+    x per Frobenius orbit of the elements of exact degree m of F_{q^m},
+    m = 2..g (as many as monic irreducibles of degree m)."""
+    q = spec.q
+    pts = q - 1
+    for m in range(2, spec.g + 1):
+        pts += sum(_mobius(m // d) * q ** d for d in range(1, m + 1) if m % d == 0) // m
+    return pts
+
+
 def table_reads(spec: JobSpec, n_squarefree: int, method: int) -> float:
     """Shared-memory table reads one launch performs for this job (expected
-    value over the family; points x != 0 of every field F_{q^k}, k <= g):
+    value over the family; the points of points_per_member):
       0, per-member Horner: one Zech read per nonzero c_i, i <= d-2, per
         point of a square-free member;
       1, fan-out over c_0 (groups of q members): per group and point, the
@@ -81,7 +118,7 @@ def table_reads(spec: JobSpec, n_squarefree: int, method: int) -> float:
         point, the chain over c_2..c_d, one Zech addition per c_1 != 0 and
         one fan-out row per c_1: chain + 2q - 1."""
     d, q = spec.degree, spec.q
-    pts = sum(q ** k - 1 for k in range(1, spec.g + 1))
+    pts = points_per_member(spec)
     if method == 2:
         return spec.n() / q ** 2 * pts * (chain_reads(spec, 2) + 2 * q - 1)
     if method == 1:
@@ -215,27 +252,40 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+def _strip_comments(text: str) -> str:
+    """C/C++ source without comments and blank space (string literals are
+    kept as they are; none of the kernel sources puts comment markers in one)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_source_hash() -> str:
+    """Hash of the CUDA sources with comments and white space removed: a
+    traffic figure stays valid across comment-only edits and lapses on any
+    change of code."""
     h = hashlib.sha256()
     src = os.path.join(ROOT, "paper_1805_11991_gb300", "csrc")
     for f in sorted(os.listdir(src)):
         if f.endswith((".cu", ".cuh")):
-            with open(os.path.join(src, f), "rb") as fh:
-                h.update(fh.read())
+            with open(os.path.join(src, f)) as fh:
+                h.update(f.encode() + b"\0" + _strip_comments(fh.read()).encode())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the count kernel from the committed ncu summary,
-    if it was taken on the current kernel source."""
+def profiled_traffic(workload: str):
+    """DRAM bytes per step of the count kernels from the committed ncu summary
+    of this workload, if it was taken on the current kernel source."""
     try:
         with open(PROFILE_TRAFFIC) as fh:
             d = json.load(fh)
     except (OSError, ValueError):
         return None
-    if d.get("kernel_source_hash") != kernel_source_hash():
+    w = d.get(workload)
+    if not w or w.get("kernel_source_hash") != kernel_source_hash():
         return None
-    return d.get("dram_bytes_per_step")
+    return w.get("dram_bytes_per_step")
 
 
 # ---------------------------------------------------------------------------
@@ -297,6 +347,71 @@ def serve_leg(hwc, jobs, batched_results, batched_evals_per_s, n_requests, load,
 # ---------------------------------------------------------------------------
 # GPU arm
 
+def _hjobs(hwc, jobs):
+    return [hwc.make_job(s.g, s.q, s.kind, s.degree, s.first, s.n(), s.seed, s.sample_count) for s in jobs]
+
+
+def _timed(batch, k, stream, flush):
+    """k steps of `batch`, each timed by CUDA events on `stream` with an L2
+    flush (outside the events) before it; returns (total ms, count-kernel ms
+    per step)."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+    kms = []
+    for a, b in ev:
+        with torch.cuda.stream(stream):
+            flush.zero_()                    # L2 flush, outside the timed events
+        a.record(stream)
+        batch.launch(stream)
+        b.record(stream)
+        kms.append(batch.kernel_ms())       # waits for this step
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev), kms
+
+
+def _workload_units(batch, jobs):
+    """(square-free evaluations, members, table reads, kernels, results) of one
+    run of a batch whose last launch has finished."""
+    results = [batch.result(i) for i in range(len(jobs))]
+    sqf = [h.n_squarefree for h in results]
+    methods = [batch.job_method(i) for i in range(len(jobs))]
+    units = sum(n * evals_per_member(s) for n, s in zip(sqf, jobs))
+    members = sum(s.n() for s in jobs)
+    reads = sum(table_reads(s, n, m) for n, s, m in zip(sqf, jobs, methods))
+    kernels = sorted({KERNELS[m] for m in methods})
+    return units, members, reads, kernels, results
+
+
+def extra_workload(hwc, name, steps, warmup, stream, flush, plain=True):
+    """One more workload on this GPU, batched (graph) and optionally plain,
+    with its own device times; returns (summary dict, batched results)."""
+    jobs = CONFIGS[name]()
+    hj = _hjobs(hwc, jobs)
+    batched = hwc.Batch(hj, flags=hwc.FLAG_GRAPH | hwc.FLAG_TIMING)
+    pl = hwc.Batch(hj, flags=hwc.FLAG_PLAIN | hwc.FLAG_TIMING) if plain else None
+    for _ in range(warmup):
+        batched.launch(stream)
+        if pl:
+            pl.launch(stream)
+    import torch
+    torch.cuda.synchronize()
+    units, members, reads, kernels, results = _workload_units(batched, jobs)
+    ms, kms = _timed(batched, steps, stream, flush)
+    out = {"jobs": len(jobs), "members": members, "steps": steps, "warmup": warmup,
+           "batched": {"value": units * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+                       "kernel_ms": statistics.mean(kms), "curves_per_s": members * steps / (ms * 1e-3),
+                       "launches_per_step": batched.kernel_launches(),
+                       "table_reads_per_s": reads / (statistics.mean(kms) * 1e-3), "kernels": kernels}}
+    if pl:
+        pms, pkms = _timed(pl, steps, stream, flush)
+        out["plain"] = {"value": units * steps / (pms * 1e-3), "unit": UNIT, "ms_per_step": pms / steps,
+                        "kernel_ms": statistics.mean(pkms), "launches_per_step": pl.kernel_launches()}
+        out["batched_over_plain"] = out["batched"]["value"] / out["plain"]["value"]
+        pl.close()
+    batched.close()
+    return out, jobs, results
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -313,10 +428,15 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
 
-    from paper_1805_11991_gb300 import hwc
+    from paper_1805_11991_gb300 import hwc, shard
 
-    jobs = CONFIGS[args.config]()        # every rank runs the whole workload (weak scaling)
-    hjobs = [hwc.make_job(s.g, s.q, s.kind, s.degree, s.first, s.n(), s.seed, s.sample_count) for s in jobs]
+    full_jobs = CONFIGS[args.config]()
+    # each rank takes a contiguous shard of every job's member range
+    jobs = []
+    for s in full_jobs:
+        a, n = shard.shard_range(s.first, s.n(), rank, world)
+        jobs.append(s.with_range(a, n))
+    hjobs = _hjobs(hwc, jobs)
     batched = hwc.Batch(hjobs, flags=hwc.FLAG_GRAPH | hwc.FLAG_TIMING)
     plain = hwc.Batch(hjobs, flags=hwc.FLAG_PLAIN | hwc.FLAG_TIMING)
     stream = torch.cuda.Stream()
@@ -331,38 +451,20 @@ def main():
         batched.launch(stream)
         plain.launch(stream)
     torch.cuda.synchronize()
-    results = [batched.result(i) for i in range(len(jobs))]
-    sqf = [h.n_squarefree for h in results]
-    units = sum(n * evals_per_member(s) for n, s in zip(sqf, jobs))
-    members = sum(s.n() for s in jobs)
-    methods = [batched.job_method(i) for i in range(len(jobs))]
-    lookups = sum(table_reads(s, n, m) for n, s, m in zip(sqf, jobs, methods))
-    kernels = sorted({KERNELS[m] for m in methods})
-
-    def timed(batch, k):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
-        kms = []
-        for a, b in ev:
-            with torch.cuda.stream(stream):
-                flush.zero_()                    # L2 flush, outside the timed events
-            a.record(stream)
-            batch.launch(stream)
-            b.record(stream)
-            kms.append(batch.kernel_ms())       # waits for this step
-        torch.cuda.synchronize()
-        return sum(a.elapsed_time(b) for a, b in ev), kms
+    units, members, lookups, kernels, results = _workload_units(batched, jobs)
 
     barrier()
     torch.cuda.synchronize()
     with ClockSampler(local_rank) as clk:
-        total_ms, kernel_ms = timed(batched, args.steps)
+        total_ms, kernel_ms = _timed(batched, args.steps, stream, flush)
     torch.cuda.synchronize()
     barrier()
-    plain_ms, plain_kms = timed(plain, args.steps)
+    plain_ms, plain_kms = _timed(plain, args.steps, stream, flush)
 
     # e2e through the public API: launch + copy back + sort every job's histogram
     e2e_steps = max(3, args.steps // 2)
     torch.cuda.synchronize()
+    barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         batched.launch(stream)
@@ -371,10 +473,14 @@ def main():
     e2e_s = time.perf_counter() - t0
     h2d, d2h = batched.io_bytes()
 
+    all_units, all_members = units, members
     if dist is not None:
         t = torch.tensor([total_ms, plain_ms, e2e_s], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms, plain_ms, e2e_s = (float(v) for v in t.tolist())
+        u = torch.tensor([units, members], device="cuda", dtype=torch.float64)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        all_units, all_members = (float(v) for v in u.tolist())
 
     # roofline of the dominant kernel (the persistent count kernel)
     kern_ms = statistics.mean(kernel_ms)
@@ -389,39 +495,65 @@ def main():
         pass
     sm_max = sm_max or 2070.0
     peak = sms * sm_max * 1e6 * 32 / 1e9          # one 32-lane LDS wavefront per SM per clock
-    table_entries = 2 * (31 ** 2 - 1) + 1
+    table_entries = 2 * (27 ** 3 - 1) + 1 if args.config == "config4" else 2 * (31 ** 2 - 1) + 1
     measured = hwc.probe_smem_gather(table_entries, 4096) / 1e9
-    traffic = profiled_traffic()
+    traffic = profiled_traffic(args.config)
 
-    value = world * units * args.steps / (total_ms * 1e-3)
+    value = all_units * args.steps / (total_ms * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic: full coefficient families decoded on the device",
-        "config": {"workload": args.config, "jobs": [f"g{s.g} q{s.q} d{s.degree} members {s.n()}" for s in jobs],
-                   "members": members, "squarefree": sum(sqf), "l2": "flushed (512 MiB write) between steps",
-                   "launch": "persistent kernel in a CUDA graph"},
-        "curves_per_s": world * members * args.steps / (total_ms * 1e-3),
-        "plain": {"value": world * units * args.steps / (plain_ms * 1e-3), "unit": UNIT,
+        "config": {"workload": args.config,
+                   "jobs": [f"g{s.g} q{s.q} d{s.degree} members {s.n()}" for s in full_jobs],
+                   "members": int(all_members), "squarefree_evals_per_step": int(all_units),
+                   "l2": "flushed (512 MiB write) between steps",
+                   "launch": "persistent kernel in a CUDA graph",
+                   "sharding": f"each job's members split into {world} contiguous shards" if world > 1 else None},
+        "curves_per_s": all_members * args.steps / (total_ms * 1e-3),
+        "plain": {"value": all_units * args.steps / (plain_ms * 1e-3), "unit": UNIT,
                   "ms_per_step": plain_ms / args.steps, "launches_per_step": plain.kernel_launches()},
-        "e2e": {"value": world * units * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": all_units * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps * batched.kernel_launches(),
         "roofline": {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "Glookup/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "+".join(kernels),
-                     "kernel_ms": kern_ms,
+                     "kernel_ms": kern_ms, "table_reads_per_step": lookups,
                      "peak_source": f"{sms} SMs x {sm_max:.0f} MHz x 32 lanes (bank-conflict-free LDS)",
                      "measured_random_gather": measured,
                      "frac_of_measured_random_gather": achieved / measured},
     }
+    if world > 1:
+        # merge every job's shards (after the timed region) and check them against
+        # one GPU counting the whole job
+        merged = [shard.gather_merge(h) for h in results]
+        if rank == 0:
+            single = hwc.Batch(_hjobs(hwc, full_jobs), flags=hwc.FLAG_GRAPH)
+            single.launch(stream)
+            torch.cuda.synchronize()
+            same = True
+            for i, m in enumerate(merged):
+                h = single.result(i)
+                same &= (m.counts.shape == h.counts.shape and bool((m.counts == h.counts).all())
+                         and bool((m.mult == h.mult).all()) and m.n_total == h.n_total)
+            single.close()
+            line["shards_match_single_gpu"] = bool(same)
+    if rank == 0 and world == 1 and not args.no_extras:
+        ew = max(1, min(args.warmup, 3))
+        line["config3"], _, _ = extra_workload(hwc, "config3", args.extra_steps, ew, stream, flush)
+        c2, c2_jobs, c2_results = extra_workload(hwc, "config2", args.steps, ew, stream, flush, plain=False)
+        line["config2"] = c2
+        line["served"] = serve_leg(hwc, c2_jobs, c2_results, c2["batched"]["value"], args.serve_requests,
+                                   args.serve_load)
+        line["served"]["workload"] = "config2"
+    if args.serve and rank == 0 and world == 1:
+        line["served_" + args.config] = serve_leg(hwc, jobs, results, value, args.serve_requests, args.serve_load)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r, c, threads, sample = oracle_rate(jobs, args.cpu_seconds)
         r1, _, _, sample1 = oracle_rate(jobs, 4.0, offset_frac=0.5, threads=1)   # the paper's CPU column is 1 core
         line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": sample, "curves_per_s": c, "value_1core": r1, "sample_1core": sample1}
-    if args.serve and rank == 0:
-        line["served"] = serve_leg(hwc, jobs, results, value / world, args.serve_requests, args.serve_load)
     line["clocks"] = clk.summary()
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -138,6 +138,24 @@ int hwc_family_size(uint32_t q, const hwc_family_t *fam, uint64_t *n);
 #define HWC_FLAG_TIMING 0x10u     /* time the count kernel(s) with CUDA events */
 #define HWC_FLAG_FAN1 0x20u       /* one-level c_0 fan-out even where the
                                      two-level (c_1, c_0) kernel applies */
+/* By default the kernels evaluate f at one point per Frobenius orbit: x and
+ * x^q, x^(q^2), ... give the same chi(f(x)) because f has coefficients in
+ * F_q, so F_{q^k} is covered by the elements of exact degree m | k, one per
+ * orbit of m conjugates, each weighted by m (and chi_{q^k} = chi_{q^m}^(k/m)
+ * on F_{q^m}).  The counts are the same as evaluating every point. */
+#define HWC_FLAG_ALL_POINTS 0x40u /* evaluate every x of every F_{q^k} instead */
+/* Key the histogram also by the factorisation pattern lambda(f) of eq. 1.2:
+ * the partition of 2g+2 formed by the degrees of the irreducible factors of
+ * f over F_q, with one more part 1 when deg f = 2g+1 (read the patterns with
+ * hwc_hist_lambda).  The kernels get the factors of degree m <= g from the
+ * zeros of f at the Frobenius-orbit points of exact degree m (one per
+ * irreducible factor of degree m), the rest from the degree left over and,
+ * when 2g+2 is left (one factor of degree 2g+2 or two of degree g+1), from
+ * the quadratic character of the discriminant of f (Stickelberger: the
+ * number of irreducible factors r of a square-free f has
+ * (-1)^(deg f - r) = chi(disc f)).  Runs the per-member kernel; not with
+ * HWC_FLAG_ALL_POINTS. */
+#define HWC_FLAG_LAMBDA 0x80u
 
 /* Histogram of (#C(F_q), ..., #C(F_{q^g})) over the square-free members
  * [first, first+count) of the family (Algorithm 1: point counts and the
@@ -158,7 +176,12 @@ int hwc_count_members(uint32_t g, uint32_t q, const hwc_family_t *fam,
                       uint64_t first, uint64_t count, int unfiltered, uint32_t flags,
                       void *stream, int32_t *counts, uint8_t *sqf);
 
-/* Histogram contents.  n_entries distinct tuples; n_squarefree = sum of the
+/* Histograms.  A histogram is the multiset of tuples (#C_1..#C_g), one per
+ * square-free member, i.e. the map N_{g,q} of eq. 1.2 with every weight 1 and
+ * the tuple keyed by #C_k = q^k + 1 - a_k (eq. 1.1) instead of a_k, without the
+ * factorisation partition.  Histograms of disjoint member ranges add.
+ *
+ * Contents: n_entries distinct tuples; n_squarefree = sum of the
  * multiplicities; n_total = members examined. */
 int hwc_hist_size(const hwc_hist_t *h, uint64_t *n_entries, uint64_t *n_squarefree,
                   uint64_t *n_total);
@@ -167,7 +190,13 @@ int hwc_hist_genus(const hwc_hist_t *h, uint32_t *g);
 /* Host arrays: counts[n_entries*g] (#C_1..#C_g per entry, sorted
  * lexicographically), mult[n_entries]. */
 int hwc_hist_read(const hwc_hist_t *h, int32_t *counts, uint64_t *mult);
-/* into += from (same g); shards of one family and resumed runs add up. */
+/* Factorisation patterns of a histogram counted with HWC_FLAG_LAMBDA:
+ * codes[n_entries], entry i's lambda as sum_m n_m 16^(m-1), n_m the parts
+ * equal to m (m = 1..2g+2).  Entries are then sorted by code, then by tuple.
+ * HWC_ERR_STATE for a histogram without patterns. */
+int hwc_hist_lambda(const hwc_hist_t *h, uint64_t *codes);
+/* into += from (same g, both with or both without patterns); shards of one
+ * family and resumed runs add up. */
 int hwc_hist_merge(hwc_hist_t *into, const hwc_hist_t *from);
 /* New histogram from host arrays (e.g. a checkpoint), same layout as read. */
 int hwc_hist_from_arrays(uint32_t g, uint64_t n_entries, const int32_t *counts,
@@ -176,6 +205,9 @@ void hwc_hist_free(hwc_hist_t *h);
 
 /* ------------------------------------------------------------------ */
 /* Batched execution: many jobs in one persistent launch               */
+/* The paper launches one kernel per curve and field (Sec. 3.3); batching
+ * many jobs of uneven size into one launch has no counterpart there.  Each
+ * job's histogram is the one hwc_count gives for it alone. */
 
 /* Prepare a batch: builds (or reuses) the field tables of every job,
  * allocates one device histogram per job and the work queue, and picks the
@@ -220,6 +252,8 @@ int hwc_batch_run(const hwc_job_t *jobs, size_t n_jobs, uint32_t flags, void *st
 
 /* ------------------------------------------------------------------ */
 /* Serving: a request loop with continuous batching                    */
+/* No counterpart in the paper (its runs are offline).  Each request's
+ * histogram is the one hwc_count gives for the same job alone. */
 
 typedef struct {
     uint64_t device_bytes;   /* admission budget for tables + histograms    */

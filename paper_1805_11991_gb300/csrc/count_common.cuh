@@ -19,6 +19,22 @@ struct TabP {   // staged two-level Zech table: index u at u + 64; PAD: entry i 
     __device__ __forceinline__ uint32_t at(uint32_t i) const { return PAD ? t[i + ((i >> 6) << 1)] : t[i]; }
     __device__ __forceinline__ uint32_t operator[](uint32_t u) const { return at(u + kFan2Prefix); }
 };
+// 17-bit Zech table in shared memory (fields whose logs exceed 16 bits): the
+// low 16 bits of entry v in lo[v], bit 16 in bit v of the plane hi.  Read with
+// the doubled index range of TabS / TabG: u in [0, 2L] folds to v in [0, L] by
+// one subtraction; entries L/2 and L hold the marker 0x1FFFF, returned as the
+// poison 2L.
+struct Tab17 {
+    const uint16_t *lo;
+    const uint32_t *hi;
+    uint32_t L;
+    __device__ __forceinline__ uint32_t operator[](uint32_t u) const
+    {
+        const uint32_t v = min(u, u - L);
+        const uint32_t w = (uint32_t)lo[v] | (((hi[v >> 5] >> (v & 31u)) & 1u) << 16);
+        return w == 0x1FFFFu ? 2 * L : w;
+    }
+};
 struct TabG {   // u32 table in global memory (L1/L2 resident)
     const uint32_t *t;
     __device__ __forceinline__ uint32_t operator[](uint32_t u) const { return __ldg(t + u); }
@@ -148,6 +164,60 @@ __device__ bool squarefree(const FqLog<Tab> &F, const uint32_t *coef1, uint32_t 
     return dg[a] == 0;
 }
 
+// Quadratic character of the discriminant of a square-free f over F_q (logs of
+// the coefficients as in squarefree(); f' is taken with its true degree e):
+//     disc f = (-1)^(d(d-1)/2) lc(f)^(-1) Res_{d,d-1}(f, f'),
+//     Res_{d,d-1}(f, f') = lc(f)^(d-1-e) Res_{d,e}(f, f'),
+// and Res_{d,e} by Euclid's algorithm, Res(A, B) = (-1)^(ab) lc(B)^(a-r) Res(B, A mod B)
+// (r = deg(A mod B)), Res(A, c) = c^a for a constant c.  chi of a product is
+// the product of the chi: the parity of the logs, and chi(-1) = (-1)^((q-1)/2).
+// Returns +1 or -1.
+template <int D, class Tab>
+__device__ int disc_chi(const FqLog<Tab> &F, const uint32_t *coef1, uint32_t p, uint32_t q,
+                        const uint32_t (&c)[D + 1])
+{
+    const uint32_t Z = F.L;
+    const uint32_t neg1 = ((q - 1) / 2) & 1u;   // parity of chi(-1)
+    uint32_t P[2][D + 1];
+    int dg[2];
+    for (int i = 0; i <= D; ++i) P[0][i] = coef1[c[i]];
+    for (int i = 1; i <= D; ++i) P[1][i - 1] = F.mul(coef1[i % p], P[0][i]);
+    P[1][D] = Z;
+    dg[0] = D;
+    dg[1] = D - 1;
+    while (dg[0] >= 0 && P[0][dg[0]] == Z) --dg[0];
+    while (dg[1] >= 0 && P[1][dg[1]] == Z) --dg[1];
+    const int d = dg[0], e = dg[1];
+    // (-1)^(d(d-1)/2) lc(f)^(-1) lc(f)^(d-1-e): parity of the log of lc(f) counts d - e times
+    uint32_t par = (((uint32_t)(d * (d - 1) / 2)) & 1u) * neg1;
+    par ^= (P[0][d] & 1u) * ((uint32_t)(d - e) & 1u);
+    int a = 0, b = 1;
+    for (;;) {
+        const int da = dg[a], db = dg[b];
+        if (db == 0) {   // Res(A, c) = c^a
+            par ^= (P[b][0] & 1u) * ((uint32_t)da & 1u);
+            break;
+        }
+        const uint32_t lb = P[b][db];
+        const uint32_t il = (F.L - lb) % F.L;
+        for (int t = da; t >= db; --t) {
+            if (P[a][t] == Z) continue;
+            const uint32_t cf = F.mul(P[a][t], il);
+            for (int i = 0; i <= db; ++i) P[a][t - db + i] = F.add(P[a][t - db + i], F.neg(F.mul(cf, P[b][i])));
+        }
+        int dr = db - 1;
+        while (dr >= 0 && P[a][dr] == Z) --dr;
+        // f square-free: the remainder sequence ends in a nonzero constant
+        par ^= (((uint32_t)(da * db)) & 1u) * neg1;
+        par ^= (lb & 1u) * ((uint32_t)(da - dr) & 1u);
+        dg[a] = dr;
+        const int tmp = a;
+        a = b;
+        b = tmp;
+    }
+    return par ? -1 : 1;
+}
+
 // ---------------------------------------------------------------------
 // one field: sum over x in F_Q^x of chi(f(x)) for this lane's share of x
 //
@@ -211,13 +281,48 @@ struct WarpStats {
     uint32_t examined = 0, sqf = 0;
 };
 
+// S_k = sum over x in F_{q^k} of chi_{q^k}(f(x)) from the sums of the fields'
+// points.  With one point per Frobenius orbit (J.reps[1] set): chi(f(x)) is
+// constant on the orbit {x, x^q, ...} (f has coefficients in F_q), an element
+// of exact degree m has m conjugates, and chi_{q^k}(y) = chi_{q^m}(y)^(k/m) for
+// y in F_{q^m}, so
+//     S_k = sum_{m | k} m * (E_m if k/m is odd, else N_m - Z_m),
+// E_m = sum of chi_{q^m}(f(x)), Z_m = number of zeros of f, N_m = number of
+// points, over the orbit points of exact degree m (x = 0 belongs to m = 1).
+// Every point evaluated (J.reps[1] null): S_k = E_k.
+template <int G>
+__device__ __forceinline__ void orbit_combine(const KJob &J, const int (&E)[G], const int (&Z)[G], int (&S)[G])
+{
+    const bool orb = G >= 2 && J.reps[G >= 2 ? 1 : 0] != nullptr;
+#pragma unroll
+    for (int k = 1; k <= G; ++k) {
+        if (!orb) {
+            S[k - 1] = E[k - 1];
+            continue;
+        }
+        int s = 0;
+#pragma unroll
+        for (int m = 1; m <= k; ++m) {
+            if (k % m) continue;
+            const int Nm = m == 1 ? (int)J.q : (int)J.npts[m - 1];
+            s += m * (((k / m) & 1) ? E[m - 1] : Nm - Z[m - 1]);
+        }
+        S[k - 1] = s;
+    }
+}
+
 // copy the job's tables into shared memory (all threads of the CTA)
 __device__ void stage_job(const KJob &J, uint8_t *smem)
 {
     uint16_t *s16 = reinterpret_cast<uint16_t *>(smem);
     uint32_t *s32 = reinterpret_cast<uint32_t *>(smem);
     for (uint32_t k = 0; k < J.g; ++k) {
-        if (J.tab_kind[k] != kTabDoubleGlobal) {
+        if (J.tab_kind[k] == kTab17Smem) {   // low halves, then the plane of high bits
+            uint16_t *dst = s16 + J.tab_off[k];
+            for (uint32_t i = threadIdx.x; i <= J.L[k]; i += blockDim.x) dst[i] = J.z17lo[k][i];
+            uint32_t *dhi = reinterpret_cast<uint32_t *>(s16 + J.tab_hi_off[k]);
+            for (uint32_t i = threadIdx.x; i < (J.L[k] + 32) / 32; i += blockDim.x) dhi[i] = J.z17hi[k][i];
+        } else if (J.tab_kind[k] != kTabDoubleGlobal) {
             const bool tri = J.tab_kind[k] == kTabTripleSmem;
             const uint32_t n = (tri ? 3 : 2) * J.L[k] + 1;
             const uint16_t *src = tri ? J.zech3[k] : J.zech2[k];

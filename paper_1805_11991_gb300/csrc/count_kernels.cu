@@ -86,9 +86,9 @@ KernelFn fan2_kernel(int D)
     return D <= 6 ? fan2_kernel_a(D) : fan2_kernel_b(D);
 }
 
-static KernelFn persistent_fn(int D)
+static KernelFn persistent_fn(int D, int block = 256)
 {
-    return horner_kernel(D, 1);
+    return horner_kernel(D, block > 256 ? 3 : 1);
 }
 
 int prepare_count_kernels(void)
@@ -101,7 +101,8 @@ int prepare_count_kernels(void)
     if (dev >= 0 && dev < 64 && done[dev]) return HWC_OK;
     const int optin = (int)device_smem_optin();
     for (int D = 3; D <= kMaxD; ++D) {
-        for (KernelFn fn : {persistent_fn(D), fan_kernel(D, 1, true), fan_kernel(D, 2, true), fan2_kernel(D)}) {
+        for (KernelFn fn : {persistent_fn(D), persistent_fn(D, 768), fan_kernel(D, 1, true), fan_kernel(D, 2, true),
+                            fan2_kernel(D)}) {
             if (!fn) continue;   // no kernel for this degree and row width
             cudaFuncAttributes fa{};
             HWC_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));   // static smem counts against the limit
@@ -129,19 +130,21 @@ uint32_t device_smem_optin(void)
     return n > 0 ? (uint32_t)n : 48u * 1024u;
 }
 
-static KernelFn kernel_for(int D, uint32_t method, uint32_t words, bool persistent)
+// the per-member kernel has two instantiations: up to 256 threads per CTA, and
+// up to 768 (chosen by the block size)
+static KernelFn kernel_for(int D, uint32_t method, uint32_t words, bool persistent, int block)
 {
     if (method == 2) return fan2_kernel(D);
     if (method == 1) return fan_kernel(D, (int)words, persistent);
     (void)persistent;   // every run is a persistent launch (a plain run has one job per launch)
-    return persistent_fn(D);
+    return persistent_fn(D, block);
 }
 
 int max_ctas_per_sm(int D, uint32_t method, uint32_t words, int block, uint32_t smem_bytes,
                     bool persistent, int *out)
 {
     int n = 0;
-    KernelFn fn = kernel_for(D, method, words, true);
+    KernelFn fn = kernel_for(D, method, words, true, block);
     if (!fn) return set_error(HWC_ERR_ARG, "degree %d has no kernel", D);
     cudaFuncAttributes fa{};
     HWC_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
@@ -168,7 +171,7 @@ int launch_persistent(int D, uint32_t method, uint32_t words, const KJob *d_jobs
                       unsigned long long *d_counter, uint32_t max_smem, const LaunchShape &sh,
                       cudaStream_t s)
 {
-    KernelFn fn = kernel_for(D, method, words, true);
+    KernelFn fn = kernel_for(D, method, words, true, sh.block);
     if (!fn) return set_error(HWC_ERR_ARG, "degree %d has no kernel", D);
     uint32_t item_tiles = (uint32_t)sh.item_tiles;
     void *args[] = {(void *)&d_jobs, (void *)&d_item_start, (void *)&n_jobs, (void *)&n_items,
@@ -322,10 +325,16 @@ extern "C" int hwc_count_noalloc(uint32_t g, uint32_t q, const hwc_family_t *fam
     for (uint32_t i = 0; i + 1 < d; ++i) kj.fam_mz *= q;
     kj.qd = kj.fam_mz * q;
     kj.n_tiles = (count + kTileMembers - 1) / kTileMembers;
+    int dev = 0;
+    HWC_CUDA_TRY(cudaGetDevice(&dev));
     for (uint32_t k = 1; k <= g; ++k) {
         const hwc_tables_t *h = tables[k - 1];
         if (!h || !h->t || h->t->q != q || h->t->k != k)
             return set_error(HWC_ERR_ARG, "tables[%u] must be the tables of F_%u^%u", k - 1, q, k);
+        // a handle built on another device holds that device's pointers
+        if (h->t->device != dev)
+            return set_error(HWC_ERR_ARG, "tables[%u] were built on device %d, the current device is %d", k - 1,
+                             h->t->device, dev);
         const Tables *t = h->t;
         kj.Q[k - 1] = t->Q;
         kj.L[k - 1] = t->L;
@@ -334,6 +343,9 @@ extern "C" int hwc_count_noalloc(uint32_t g, uint32_t q, const hwc_family_t *fam
         kj.zech3[k - 1] = t->d_zech3;
         kj.zech2w[k - 1] = t->d_zech2w;
         kj.coef_log[k - 1] = t->d_coef_log;
+        kj.z17lo[k - 1] = t->d_z17lo;
+        kj.z17hi[k - 1] = t->d_z17hi;
+        set_points(kj, k, t, true);
     }
     layout_job_smem(kj, device_smem_optin() - 4096);
     unsigned char *scratch = nullptr;

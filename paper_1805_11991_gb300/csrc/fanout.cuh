@@ -352,22 +352,27 @@ __device__ bool squarefree_digits(const uint8_t *mulT, const uint8_t *subT, cons
 }
 
 // per-member counts of one field for the whole group: lane c gets sum_x chi(f_c(x))
-// for c = lane (and lane + 32), from n_0, the row-bit counts and z_c
+// for c = lane (and lane + 32), from n_0, the row-bit counts and z_c.  The
+// points are x = alpha^j for j = pts[i], i < np (one per Frobenius orbit), or
+// every j < L when pts is null.
 template <int D, int W, bool TRIPLE, class Tab>
 __device__ __forceinline__ void group_field(const Tab T, const KJob &J, int k, const uint8_t *smem,
                                             const HChain<D> &H, const uint32_t (&lam)[D + 1], uint32_t nz,
                                             uint32_t *zc, int lane, uint32_t &n0, uint32_t (&cnt)[W])
 {
     const uint32_t L = J.L[k];
+    const uint32_t *__restrict__ pts = J.reps[k];
+    const uint32_t np = J.npts[k];
+    auto point = [&](uint32_t i) -> uint32_t { return pts ? __ldg(pts + i) : i; };
     const uint8_t *rows = smem + J.row_off[k];
     const uint8_t *zdig = smem + J.zdig_off[k];
     const uint32_t zdiv = J.zdiv[k];
     const uint32_t bar = J.barrett[k];
-    if (L <= 64) {   // tiny field (k = 1): one pair of x per lane, counts < 4
+    if (np <= 64) {   // few points (F_q, or a small orbit list): one pair of x per lane, counts < 4
         const uint32_t jA = lane, jB = lane + 32;
-        const bool vA = jA < L, vB = jB < L;
+        const bool vA = jA < np, vB = jB < np;
         uint32_t yA, yB;
-        log_y_pair<D, TRIPLE>(T, L, bar, H, lam, nz, vA ? jA : 0, vB ? jB : 0, yA, yB);
+        log_y_pair<D, TRIPLE>(T, L, bar, H, lam, nz, vA ? point(jA) : 0, vB ? point(jB) : 0, yA, yB);
         uint32_t mA[W], mB[W];
         row_of<W>(rows, zdig, zdiv, L, yA, vA, mA, n0, zc);
         row_of<W>(rows, zdig, zdiv, L, yB, vB, mB, n0, zc);
@@ -378,13 +383,13 @@ __device__ __forceinline__ void group_field(const Tab T, const KJob &J, int k, c
         }
         return;
     }
-    for (uint32_t c0 = 0; c0 < L; c0 += kChunkBlocks * 256) {
+    for (uint32_t c0 = 0; c0 < np; c0 += kChunkBlocks * 256) {
         Planes P[W];
 #pragma unroll
         for (int w = 0; w < W; ++w)
 #pragma unroll
             for (int b = 0; b < 8; ++b) P[w].p[b] = 0;
-        const uint32_t cend = min(L, c0 + kChunkBlocks * 256);
+        const uint32_t cend = min(np, c0 + kChunkBlocks * 256);
         for (uint32_t j0 = c0; j0 < cend; j0 += 256) {
             uint32_t a[W][8];
 #pragma unroll
@@ -392,7 +397,7 @@ __device__ __forceinline__ void group_field(const Tab T, const KJob &J, int k, c
                 const uint32_t jA = j0 + it * 64 + lane, jB = jA + 32;
                 const bool vA = jA < cend, vB = jB < cend;
                 uint32_t yA, yB;
-                log_y_pair<D, TRIPLE>(T, L, bar, H, lam, nz, vA ? jA : 0, vB ? jB : 0, yA, yB);
+                log_y_pair<D, TRIPLE>(T, L, bar, H, lam, nz, vA ? point(jA) : 0, vB ? point(jB) : 0, yA, yB);
                 uint32_t mA[W], mB[W];
                 row_of<W>(rows, zdig, zdiv, L, yA, vA, mA, n0, zc);
                 row_of<W>(rows, zdig, zdiv, L, yB, vB, mB, n0, zc);
@@ -479,10 +484,10 @@ __device__ __forceinline__ void process_group(const KJob &J, uint64_t gtile, con
         return;
     }
 
-    int32_t N[W][G];
+    int E[W][G], Zr[W][G];   // per field: sum of chi and zeros over its points (x = 0 in field 1)
 #pragma unroll
     for (int k = 0; k < G; ++k) {
-        const uint32_t L = J.L[k], Q = J.Q[k];
+        const uint32_t L = J.L[k];
         const uint32_t *coefk = s32 + J.coef_off[k];
         uint32_t lam[D + 1];
 #pragma unroll
@@ -503,19 +508,34 @@ __device__ __forceinline__ void process_group(const KJob &J, uint64_t gtile, con
             group_field<D, W, false>(TabS{s16 + J.tab_off[k]}, J, k, smem, H, lam, nz, zc, lane, n0, cnt);
         else
             group_field<D, W, false>(TabG{J.zech2w[k]}, J, k, smem, H, lam, nz, zc, lane, n0, cnt);
-        n0 = __reduce_add_sync(0xFFFFFFFFu, n0) + 1;   // + x = 0 (y = g(0) = 0)
+        // x = 0 (y = g(0) = 0) belongs to F_q, and to every field when every point is evaluated
+        const uint32_t x0 = J.reps[k] == nullptr ? 1u : 0u;
+        n0 = __reduce_add_sync(0xFFFFFFFFu, n0) + x0;
+        const uint32_t npk = J.npts[k] + x0;   // points of the field, x = 0 included
         __syncwarp();
-        int inf = 1;
-        if (D == 2 * G + 2) inf += (lam[D] & 1u) ? -1 : 1;
 #pragma unroll
         for (int w = 0; w < W; ++w) {
             const uint32_t cc = (uint32_t)lane + 32u * w;
             const uint32_t lc = cc < q ? coefk[cc] : L;
             const int chi_c = (lc == L) ? 0 : ((lc & 1u) ? -1 : 1);
-            const int S = (int)n0 * chi_c + (int)(Q - n0) - 2 * (int)cnt[w] - (int)zc[cc];
-            N[w][k] = (int32_t)Q + S + inf;
+            // y = 0: f_c = c; y = -c != 0: f_c = 0; else chi(y + c) from the row bits
+            E[w][k] = (int)n0 * chi_c + (int)(npk - n0) - 2 * (int)cnt[w] - (int)zc[cc];
+            Zr[w][k] = cc == 0 ? (int)n0 : (int)zc[cc];
         }
         __syncwarp();   // zc is cleared for the next field
+    }
+    // #C_k = Q_k + S_k + 1 + chi(c_{2g+2})
+    int32_t N[W][G];
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        int Sk[G];
+        orbit_combine<G>(J, E[w], Zr[w], Sk);
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            int inf = 1;
+            if (D == 2 * G + 2) inf += (s32[J.coef_off[k] + c[D]] & 1u) ? -1 : 1;
+            N[w][k] = (int32_t)J.Q[k] + Sk[k] + inf;
+        }
     }
 
 #pragma unroll

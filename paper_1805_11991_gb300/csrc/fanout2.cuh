@@ -70,7 +70,7 @@ __device__ __forceinline__ void flush_planes(uint32_t (&P)[kFan2Planes], uint16_
 // L + 8 for y = 0 (digit 0).  The lane's entries sit at lane, lane + 32, ...;
 // qn = lane + 32 * (number of entries).
 __device__ __forceinline__ void drain_queue(const uint16_t *rq, uint32_t qn, int lane, const uint8_t *zdig,
-                                            uint32_t zdiv, uint32_t L, uint16_t *acc_row)
+                                            uint32_t zdiv, uint32_t L, uint16_t *acc_row, uint32_t zw)
 {
     // selects, no branches in the body
     const uint32_t zrow = L + kFan2ZeroRow;
@@ -82,16 +82,17 @@ __device__ __forceinline__ void drain_queue(const uint16_t *rq, uint32_t qn, int
         // in bounds for zr too: index <= 8 < 16 <= zdig bytes
         const uint32_t d = zdig[zdiv ? __umulhi(l, zdiv) : l];
         const uint32_t di = zr ? 0u : d;
-        acc_row[di] = (uint16_t)(acc_row[di] + 1);
+        acc_row[di] = (uint16_t)(acc_row[di] + zw);
     }
 }
 
 // z(b, c) += 1 in the group's accumulator rows (row b of chunk 0, column c):
-// one shared atomic on the u32 word that holds the u16 entry
-__device__ __forceinline__ void zinc(uint32_t *acc32, uint32_t q, uint32_t b, uint32_t c)
+// one shared atomic on the u32 word that holds the u16 entry; zw = 1, or
+// 1 + 2^s where the field's zeros are also kept apart in bits s..
+__device__ __forceinline__ void zinc(uint32_t *acc32, uint32_t q, uint32_t b, uint32_t c, uint32_t zw)
 {
     const uint32_t i = b * q + c;
-    atomicAdd(acc32 + (i >> 1), 1u << ((i & 1u) << 4));
+    atomicAdd(acc32 + (i >> 1), zw << ((i & 1u) << 4));
 }
 
 // Zero digits of one batch of points counted directly, for F_q (k = 1) and
@@ -105,13 +106,15 @@ __device__ __forceinline__ void zinc(uint32_t *acc32, uint32_t q, uint32_t b, ui
 // KF = 1: all points are in F_q, whose digits come from zdig (zdig[l] = -alpha^l).
 // KF = 2: coordinate table crd[l] = -y0 | -y1 << 8 | A << 16 | B << 24 (A = 0,
 // B = -y0 for elements of F_q, the points alpha^j with j = 0 mod (q + 1));
-// jq walks those multiples of q + 1 across batches.
-// Us holds log u(x) (>= L for u = 0) of the batch's nb points from j0.
-template <int KF>
+// jq walks those multiples of q + 1 across batches (consecutive points only:
+// with one point per Frobenius orbit of degree 2 no point lies in F_q).
+// Us holds log u(x) (>= L for u = 0) of the batch's nb points from j0; the
+// lane's own two points are xA, xB (validity vA, vB) with u = uA, uB.
+template <int KF, bool REPS>
 __device__ __forceinline__ void fan2_zero_digits(const uint32_t *Us, uint32_t j0, uint32_t nb, uint32_t L,
-                                                 uint32_t q, int lane, uint32_t uA, uint32_t uB,
-                                                 const uint8_t *fq, const uint8_t *zdig, const uint32_t *crd,
-                                                 uint32_t *acc32, uint32_t &jq)
+                                                 uint32_t q, int lane, uint32_t xA, uint32_t xB, bool vA, bool vB,
+                                                 uint32_t uA, uint32_t uB, const uint8_t *fq, const uint8_t *zdig,
+                                                 const uint32_t *crd, uint32_t *acc32, uint32_t &jq, uint32_t zw)
 {
     const uint32_t qq = q * q;
     const uint8_t *mulT = fq, *addT = fq + 2 * qq + q;
@@ -120,26 +123,28 @@ __device__ __forceinline__ void fan2_zero_digits(const uint32_t *Us, uint32_t j0
         for (uint32_t i = 0; i < nb; ++i) {
             const uint32_t lu = Us[i];
             const uint32_t nu = lu < L ? zdig[lu] : 0u, nx = zdig[j0 + i];
-            if ((uint32_t)lane < q) zinc(acc32, q, (uint32_t)lane, addT[nu * q + mulT[(uint32_t)lane * q + nx]]);
+            if ((uint32_t)lane < q)
+                zinc(acc32, q, (uint32_t)lane, addT[nu * q + mulT[(uint32_t)lane * q + nx]], zw);
         }
     } else {
-    // the lane's two points of the batch (x = j0 + lane + 32 h), both loads first
-    const uint32_t xA = j0 + (uint32_t)lane, xB = xA + 32u;
-    const bool vA = xA < j0 + nb, vB = xB < j0 + nb;
+    // both loads first
     const uint32_t tA = crd[vA ? xA : 0u], tB = crd[vB ? xB : 0u];
     uint32_t cA = crd[uA < L ? uA : 0u], cB = crd[uB < L ? uB : 0u];
     cA = uA < L ? cA : 0u;
     cB = uB < L ? cB : 0u;
     if (vA && (tA & 0xFF0000u))
         zinc(acc32, q, mulT[((cA >> 8) & 0xFFu) * q + ((tA >> 16) & 0xFFu)],
-             addT[(cA & 0xFFu) * q + mulT[((cA >> 8) & 0xFFu) * q + (tA >> 24)]]);
+             addT[(cA & 0xFFu) * q + mulT[((cA >> 8) & 0xFFu) * q + (tA >> 24)]], zw);
     if (vB && (tB & 0xFF0000u))
         zinc(acc32, q, mulT[((cB >> 8) & 0xFFu) * q + ((tB >> 16) & 0xFFu)],
-             addT[(cB & 0xFFu) * q + mulT[((cB >> 8) & 0xFFu) * q + (tB >> 24)]]);
-    for (; jq < j0 + nb; jq += q + 1) {   // x in F_q: u = u0, c = -u0 + b (-x0)
-        const uint32_t lu = Us[jq - j0];
-        const uint32_t n0 = lu < L ? (crd[lu] & 0xFFu) : 0u, nx = crd[jq] >> 24;
-        if ((uint32_t)lane < q) zinc(acc32, q, (uint32_t)lane, addT[n0 * q + mulT[(uint32_t)lane * q + nx]]);
+             addT[(cB & 0xFFu) * q + mulT[((cB >> 8) & 0xFFu) * q + (tB >> 24)]], zw);
+    if (!REPS) {
+        for (; jq < j0 + nb; jq += q + 1) {   // x in F_q: u = u0, c = -u0 + b (-x0)
+            const uint32_t lu = Us[jq - j0];
+            const uint32_t n0 = lu < L ? (crd[lu] & 0xFFu) : 0u, nx = crd[jq] >> 24;
+            if ((uint32_t)lane < q)
+                zinc(acc32, q, (uint32_t)lane, addT[n0 * q + mulT[(uint32_t)lane * q + nx]], zw);
+        }
     }
     }
 }
@@ -187,16 +192,66 @@ __device__ __forceinline__ void fan2_block(const Tab T, const uint32_t *__restri
     }
 }
 
+// One block of 8 orbit points for lane (b, s): the staged log u(x) (U) and
+// d = log u - log x (D) of each point.  y_b = u + b x = u (1 + b x / u), so
+// log y_b = log u + Z(log b - d) (eq. 2.1): one Zech read at lam_b - d and one
+// fan-out row per point, as in fan2_block, with the per-point log x folded
+// into d.  u = 0 (GEN only) is staged as U >= L and D = -log x, where
+// y_b = b x.
+template <bool GEN, bool QUEUE, class Tab>
+__device__ __forceinline__ void fan2_block_reps(const Tab T, const uint32_t *__restrict__ rows, const uint32_t *Us,
+                                                const uint32_t *Ds, uint32_t L, uint32_t lam_b, bool b0,
+                                                uint32_t okm, uint16_t *rq, uint32_t &qn, uint32_t (&a)[8])
+{
+    const uint4 w0 = *reinterpret_cast<const uint4 *>(Us);
+    const uint4 w1 = *reinterpret_cast<const uint4 *>(Us + 4);
+    const uint4 d0 = *reinterpret_cast<const uint4 *>(Ds);
+    const uint4 d1 = *reinterpret_cast<const uint4 *>(Ds + 4);
+    const uint32_t U[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+    const uint32_t Dv[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+    // staged Zech index of lam_b - d + L: in [1 + 64, 2L + 64)
+    const uint32_t C = lam_b + L + kFan2Prefix;
+    uint32_t ly[8];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        const uint32_t z = T.at(C - Dv[v]);
+        uint32_t t = U[v] + z;            // < 2L, or >= 65535 when u + b x = 0
+        t = min(t, t - L);                // < L; poisoned: >= L + 8
+        t = min(t, L + kFan2ZeroRow);     // row L + 8: y = 0
+        if (GEN) {
+            uint32_t bx = lam_b + L - Dv[v];   // u = 0: y = b x, log in (0, 2L)
+            bx = min(bx, bx - L);
+            t = (U[v] >= L) ? bx : t;
+            ly[v] = b0 ? (U[v] >= L ? L + kFan2ZeroRow : U[v]) : t;
+        } else {
+            ly[v] = b0 ? U[v] : t;        // b = 0: y = u
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < 8; ++v) a[v] = rows[ly[v]];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        if (GEN && !((okm >> v) & 1u)) a[v] = 0u;
+        if (QUEUE && (int)a[v] < 0) {
+            rq[qn] = (uint16_t)ly[v];
+            qn += 32;
+        }
+    }
+}
+
 // points of one field for the whole group (all q^2 members), lane role (b, s)
 // The chain constants (lam_i and the h chain) come from the warp's shared
 // parameters at every batch: the main loop keeps no registers for them.
 // KF = 0: zero digits through the lanes' queues; KF = 1, 2: counted directly
-// per batch (fan2_zero_digits).
-template <int D, bool TRIPLE, bool PAD, int KF>
+// per batch (fan2_zero_digits).  REPS: the points are the field's orbit list
+// J.reps[k] (J.npts[k] of them), else every x = alpha^j, j < L.  A zero of
+// f_{b,c} adds zw to its accumulator (1, or 1 + 2^s to keep the field's zeros
+// apart in bits s..).
+template <int D, bool TRIPLE, bool PAD, int KF, bool REPS>
 __device__ __forceinline__ void group2_field(const KJob &J, int k, const uint8_t *smem, const HChain<D> *gH,
-                                             const uint32_t *glam, uint32_t nz, uint32_t *Us, uint16_t *acc,
-                                             uint16_t *acc_row, uint16_t *rq, int lane, bool role, uint32_t b,
-                                             uint32_t s, uint32_t S)
+                                             const uint32_t *glam, uint32_t nz, uint32_t *Us, uint32_t *Ds,
+                                             uint16_t *acc, uint16_t *acc_row, uint16_t *rq, int lane, bool role,
+                                             uint32_t b, uint32_t s, uint32_t S, uint32_t zw)
 {
     constexpr bool QUEUE = KF == 0;
     const TabP<PAD> T{reinterpret_cast<const uint16_t *>(smem) + J.tab_off[k]};
@@ -209,67 +264,92 @@ __device__ __forceinline__ void group2_field(const KJob &J, int k, const uint8_t
     const uint32_t lam_b = (b != 0) ? coefk[b] : 0u;   // log b
     const bool b0 = b == 0;
     const bool pow2S = S == 1 || S == 2 || S == 4 || S == 8;   // 64 / S points per lane, a multiple of 8
+    const uint32_t *__restrict__ pts = J.reps[k];
+    const uint32_t np = REPS ? J.npts[k] : L;
     uint32_t P[kFan2Planes];
 #pragma unroll
     for (int p = 0; p < kFan2Planes; ++p) P[p] = 0;
     uint32_t nblk = 0, qn = (uint32_t)lane, jq = 0;
     const uint32_t *crd = reinterpret_cast<const uint32_t *>(smem + J.coord_off);
-    for (uint32_t j0 = 0; j0 < L; j0 += 64) {
+    // orbit points of the next batch, loaded one batch ahead (global memory)
+    uint32_t nxA = 0, nxB = 0;
+    if (REPS) {
+        nxA = __ldg(pts + min((uint32_t)lane, np - 1));
+        nxB = __ldg(pts + min(32u + lane, np - 1));
+    }
+    for (uint32_t j0 = 0; j0 < np; j0 += 64) {
         // log u(x) for the batch, two points per lane, staged for all lanes
-        const uint32_t xA = j0 + lane, xB = j0 + 32 + lane;
+        const uint32_t iA = j0 + lane, iB = j0 + 32 + lane;
+        const bool vA = iA < np, vB = iB < np;
+        uint32_t xA = vA ? iA : 0, xB = vB ? iB : 0;
+        if (REPS) {
+            xA = nxA;   // loaded from a clamped index: a valid point for invalid lanes too
+            xB = nxB;
+            if (j0 + 64 < np) {
+                nxA = __ldg(pts + min(j0 + 64 + lane, np - 1));
+                nxB = __ldg(pts + min(j0 + 96 + lane, np - 1));
+            }
+        }
         uint32_t uA, uB;
         {
             const HChain<D> H = *gH;
             uint32_t lam[D + 1];
 #pragma unroll
             for (int i = 0; i <= D; ++i) lam[i] = glam[i];
-            log_y_pair<D, TRIPLE, TabP<PAD>, 2>(T, L, bar, H, lam, nz, xA < L ? xA : 0, xB < L ? xB : 0, uA, uB);
+            log_y_pair<D, TRIPLE, TabP<PAD>, 2>(T, L, bar, H, lam, nz, xA, xB, uA, uB);
         }
         Us[lane] = uA;
         Us[32 + lane] = uB;
+        if (REPS) {   // d = log u - log x (mod L); u = 0: d = -log x
+            Ds[lane] = uA < L ? (uA >= xA ? uA - xA : uA + L - xA) : (xA ? L - xA : 0u);
+            Ds[32 + lane] = uB < L ? (uB >= xB ? uB - xB : uB + L - xB) : (xB ? L - xB : 0u);
+        }
         const bool uzero = __any_sync(0xFFFFFFFFu, uA >= L || uB >= L);
         __syncwarp();
-        const uint32_t nb = min(64u, L - j0);   // points in this batch
+        const uint32_t nb = min(64u, np - j0);   // points in this batch
         if (!QUEUE) {   // atomics here, plain row updates (flushes) after the barrier
-            fan2_zero_digits<KF == 0 ? 1 : KF>(Us, j0, nb, L, J.q, lane, uA, uB, smem + J.fq_off, zdig, crd,
-                                               reinterpret_cast<uint32_t *>(acc), jq);
+            fan2_zero_digits<KF == 0 ? 1 : KF, REPS>(Us, j0, nb, L, J.q, lane, xA, xB, vA, vB, uA, uB,
+                                                     smem + J.fq_off, zdig, crd, reinterpret_cast<uint32_t *>(acc),
+                                                     jq, zw);
             __syncwarp();
         }
         if (pow2S && nb == 64 && !uzero) {
             const uint32_t per = 64 / S, i0 = s * per;
-            uint32_t lb = addmod(lam_b, j0 + i0, L);
+            uint32_t lb = REPS ? 0u : addmod(lam_b, j0 + i0, L);
             for (uint32_t t0 = 0; t0 < per; t0 += 8) {
                 uint32_t a[8];
-                fan2_block<false, QUEUE>(T, rows, Us + i0 + t0, L, lb, b0, 0u, rq, qn, a);
-                lb = addmod(lb, 8u % L, L);
+                if (REPS) fan2_block_reps<false, QUEUE>(T, rows, Us + i0 + t0, Ds + i0 + t0, L, lam_b, b0, 0u, rq, qn, a);
+                else fan2_block<false, QUEUE>(T, rows, Us + i0 + t0, L, lb, b0, 0u, rq, qn, a);
+                if (!REPS) lb = addmod(lb, 8u % L, L);
                 add8_p10(P, a);
                 if (++nblk == kFan2FlushBlocks) {
                     flush_planes(P, acc_row, J.q, true);
                     nblk = 0;
                 }
                 if (QUEUE && __any_sync(0xFFFFFFFFu, qn >= 32 * (kFan2Queue - 8 + 1))) {   // more than 8 entries
-                    drain_queue(rq, qn, lane, zdig, zdiv, L, acc_row);
+                    drain_queue(rq, qn, lane, zdig, zdiv, L, acc_row, zw);
                     qn = (uint32_t)lane;
                 }
             }
         } else {
             // lane chunks of a multiple of 8 points; reads past 64 hit the
-            // zeroed slack of U and are masked
+            // zeroed slack of U and D and are masked
             const uint32_t per = (((nb + S - 1) / S) + 7) & ~7u, i0 = s * per;
-            uint32_t lb = addmod(lam_b, (j0 + i0) % L, L);
+            uint32_t lb = REPS ? 0u : addmod(lam_b, (j0 + i0) % L, L);
             for (uint32_t t0 = 0; t0 < per; t0 += 8) {
                 const int nv = role ? min(8, max(0, (int)nb - (int)(i0 + t0))) : 0;
                 const uint32_t okm = (1u << nv) - 1u;
                 uint32_t a[8];
-                fan2_block<true, QUEUE>(T, rows, Us + i0 + t0, L, lb, b0, okm, rq, qn, a);
-                lb = addmod(lb, 8u % L, L);
+                if (REPS) fan2_block_reps<true, QUEUE>(T, rows, Us + i0 + t0, Ds + i0 + t0, L, lam_b, b0, okm, rq, qn, a);
+                else fan2_block<true, QUEUE>(T, rows, Us + i0 + t0, L, lb, b0, okm, rq, qn, a);
+                if (!REPS) lb = addmod(lb, 8u % L, L);
                 add8_p10(P, a);
                 if (++nblk == kFan2FlushBlocks) {
                     flush_planes(P, acc_row, J.q, true);
                     nblk = 0;
                 }
                 if (QUEUE && __any_sync(0xFFFFFFFFu, qn >= 32 * (kFan2Queue - 8 + 1))) {   // more than 8 entries
-                    drain_queue(rq, qn, lane, zdig, zdiv, L, acc_row);
+                    drain_queue(rq, qn, lane, zdig, zdiv, L, acc_row, zw);
                     qn = (uint32_t)lane;
                 }
             }
@@ -277,23 +357,39 @@ __device__ __forceinline__ void group2_field(const KJob &J, int k, const uint8_t
         __syncwarp();   // U is rewritten by the next batch
     }
     flush_planes(P, acc_row, J.q, true);
-    if (QUEUE) drain_queue(rq, qn, lane, zdig, zdiv, L, acc_row);
+    if (QUEUE) drain_queue(rq, qn, lane, zdig, zdiv, L, acc_row, zw);
 }
 
 // group2_field for the field's Zech layout (tripled or doubled, padded or not)
+// and point set (orbit list or every point)
 template <int D, int KF>
 __device__ __forceinline__ void group2_field_tabs(const KJob &J, int k, bool tri, const uint8_t *smem,
                                                   const HChain<D> *gH, const uint32_t *glam, uint32_t nz,
-                                                  uint32_t *Us, uint16_t *acc, uint16_t *acc_row, uint16_t *rq,
-                                                  int lane, bool role, uint32_t b, uint32_t s, uint32_t S)
+                                                  uint32_t *Us, uint32_t *Ds, uint16_t *acc, uint16_t *acc_row,
+                                                  uint16_t *rq, int lane, bool role, uint32_t b, uint32_t s,
+                                                  uint32_t S, uint32_t zw)
 {
-    if (J.tab_pad[k]) {
-        if (tri) group2_field<D, true, true, KF>(J, k, smem, gH, glam, nz, Us, acc, acc_row, rq, lane, role, b, s, S);
-        else group2_field<D, false, true, KF>(J, k, smem, gH, glam, nz, Us, acc, acc_row, rq, lane, role, b, s, S);
+#define HWC_G2F(TRI, PAD, REPS)                                                                             \
+    group2_field<D, TRI, PAD, KF, REPS>(J, k, smem, gH, glam, nz, Us, Ds, acc, acc_row, rq, lane, role, b, s, S, \
+                                        zw)
+    if (KF != 1 && J.reps[k]) {   // field 1 (KF = 1) takes every point
+        if (J.tab_pad[k]) {
+            if (tri) HWC_G2F(true, true, true);
+            else HWC_G2F(false, true, true);
+        } else {
+            if (tri) HWC_G2F(true, false, true);
+            else HWC_G2F(false, false, true);
+        }
     } else {
-        if (tri) group2_field<D, true, false, KF>(J, k, smem, gH, glam, nz, Us, acc, acc_row, rq, lane, role, b, s, S);
-        else group2_field<D, false, false, KF>(J, k, smem, gH, glam, nz, Us, acc, acc_row, rq, lane, role, b, s, S);
+        if (J.tab_pad[k]) {
+            if (tri) HWC_G2F(true, true, false);
+            else HWC_G2F(false, true, false);
+        } else {
+            if (tri) HWC_G2F(true, false, false);
+            else HWC_G2F(false, false, false);
+        }
     }
+#undef HWC_G2F
 }
 
 // Square-freeness of the q members f_c = g_b + c (c in F_q) that share
@@ -414,6 +510,7 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
     uint16_t *a1s = reinterpret_cast<uint16_t *>(wsm + lay.a1_off);   // dense histogram: a_1 + 32768
     uint32_t *dense = reinterpret_cast<uint32_t *>(const_cast<uint8_t *>(smem) + J.dense_off);
     uint32_t *Us = reinterpret_cast<uint32_t *>(wsm);
+    uint32_t *Ds = reinterpret_cast<uint32_t *>(wsm + lay.ds_off);
     uint16_t *acc = reinterpret_cast<uint16_t *>(wsm + lay.acc_off);
     uint16_t *rq = reinterpret_cast<uint16_t *>(wsm + lay.rq_off);
     uint32_t *sqfw = reinterpret_cast<uint32_t *>(wsm + lay.sqf_off);
@@ -433,7 +530,10 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
 
     // square-freeness: lane b settles the q members with c_1 = b at once
     for (uint32_t t = lane; t < nw; t += 32) sqfw[t] = 0;
-    if (64 + (uint32_t)lane < lay.us) Us[64 + lane] = 0;   // slack read by 8-point blocks past 64
+    if (64 + (uint32_t)lane < lay.us) {   // slack read by 8-point blocks past 64
+        Us[64 + lane] = 0;
+        Ds[64 + lane] = 0;
+    }
     if (lane == 0) {
 #pragma unroll
         for (int i = 0; i <= D; ++i) gc[i] = c[i];
@@ -489,6 +589,10 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
     const uint32_t s = role ? (uint32_t)lane / q : 0;
     uint16_t *acc_row = acc + (uint32_t)lane * q;   // lanes past S q: rows no member reads
     const uint32_t acc_words = 16 * q;
+    // one point per Frobenius orbit: S_k = sum_{m | k} m (E_m or N_m - Z_m)
+    // (orbit_combine); each member's partial sums of the later S_k wait in its
+    // key slots (or, with the dense box, next to a_1)
+    const bool orb = G >= 2 && J.reps[G >= 2 ? 1 : 0] != nullptr;
 
 #pragma unroll 1
     for (int k = 0; k < G; ++k) {
@@ -507,23 +611,29 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
         for (uint32_t m = lane; m < acc_words; m += 32) reinterpret_cast<uint32_t *>(acc)[m] = 0;
         __syncwarp();
         const bool tri = J.tab_kind[k] == kTabTripleSmem;
+        const uint32_t zs = J.zshift[k];
+        const uint32_t zw = zs ? 1u + (1u << zs) : 1u;
         // zero digits: counted directly in F_q and F_{q^2} (with its coordinates)
         // when g <= 2; queued for g >= 3, whose time is in F_{q^3} and up (one
         // copy of the field loop for every field keeps the instruction cache warm)
         // (degrees 2g+1, 2g+2 >= 7 are g >= 3: no direct copies compiled)
         const int kf = J.g > 2 ? 0 : (k == 0 ? 1 : (J.coord_off ? 2 : 0));
         if constexpr (D <= 6) {
-            if (kf == 1) group2_field_tabs<D, 1>(J, k, tri, smem, gH, glam, nz, Us, acc, acc_row, rq, lane, role, b, s, S);
-            else if (kf == 2) group2_field_tabs<D, 2>(J, k, tri, smem, gH, glam, nz, Us, acc, acc_row, rq, lane, role, b, s, S);
-            else group2_field_tabs<D, 0>(J, k, tri, smem, gH, glam, nz, Us, acc, acc_row, rq, lane, role, b, s, S);
+            if (kf == 1) group2_field_tabs<D, 1>(J, k, tri, smem, gH, glam, nz, Us, Ds, acc, acc_row, rq, lane, role, b, s, S, zw);
+            else if (kf == 2) group2_field_tabs<D, 2>(J, k, tri, smem, gH, glam, nz, Us, Ds, acc, acc_row, rq, lane, role, b, s, S, zw);
+            else group2_field_tabs<D, 0>(J, k, tri, smem, gH, glam, nz, Us, Ds, acc, acc_row, rq, lane, role, b, s, S, zw);
         } else {
             (void)kf;
-            group2_field_tabs<D, 0>(J, k, tri, smem, gH, glam, nz, Us, acc, acc_row, rq, lane, role, b, s, S);
+            group2_field_tabs<D, 0>(J, k, tri, smem, gH, glam, nz, Us, Ds, acc, acc_row, rq, lane, role, b, s, S, zw);
         }
         __syncwarp();
-        // sum_x chi(f_{b,c}(x)) = (L - sum_s acc[s q + b][c]) + chi(c)   (x = 0: y = 0)
+        // over the field's points: sum chi(f_{b,c}) = (points - (2 cnt + z)) + chi(c) for x = 0,
+        // which belongs to F_q (and to every field when every point is evaluated)
         int inf = 1;
         if (D == 2 * G + 2) inf += (glam[D] & 1u) ? -1 : 1;
+        const bool x0 = J.reps[k] == nullptr;
+        const int npts = (int)J.npts[k];
+        const int Nm = npts + (x0 ? 1 : 0);
         if ((uint32_t)lane < q) {
             const uint32_t cc = (uint32_t)lane;
             const uint32_t lc = coefk[cc];
@@ -532,7 +642,18 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
                 const uint32_t m = bb * q + cc;
                 uint32_t tot = 0;
                 for (uint32_t ss = 0; ss < S; ++ss) tot += acc[(ss * q + bb) * q + cc];
-                const int N = (int)Q + ((int)L - (int)tot + chi_c) + inf;
+                const int a2 = zs ? (int)(tot & ((1u << zs) - 1u)) : (int)tot;
+                const int E = npts - a2 + (x0 ? chi_c : 0);
+                const int Z = (zs ? (int)(tot >> zs) : 0) + ((x0 && cc == 0) ? 1 : 0);
+                // partial sum of S_{k+1} from the smaller fields, then this field's share
+                int Sk = E;
+                if (orb) {
+                    int part = 0;
+                    if (J.dense_off) part = k == 1 ? (int)(a1s[m] >> 8) : 0;
+                    else if (k > 0) part = (int16_t)(uint16_t)(keys[m] >> (16 * k));
+                    Sk = part + (k + 1) * E;
+                }
+                const int N = (int)Q + Sk + inf;
                 if (J.member_counts) {
                     const uint64_t idx = base + m;
                     if (idx >= J.first && idx < J.first + J.count) {
@@ -544,11 +665,12 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
                 const int a = (int)Q + 1 - N;   // eq. 1.1
                 const uint32_t a16 = (uint32_t)(a + 32768) & 0xFFFFu;
                 if (J.dense_off) {
-                    // g <= 2: a_1 waits in shared memory; the last field counts the member
+                    // g <= 2: a_1 (and, with orbits, the field-1 part N_1 - Z_1 of S_2)
+                    // wait in shared memory; the last field counts the member
                     if (k + 1 < G) {
-                        a1s[m] = (uint16_t)a16;
+                        a1s[m] = (uint16_t)(((uint32_t)(a + 128) & 0xFFu) | (orb ? (uint32_t)(Nm - Z) << 8 : 0u));
                     } else if (!J.member_counts && ((sqfw[m / 32] >> (m % 32)) & 1u)) {
-                        const uint32_t k1 = G == 2 ? a1s[m] : a16;
+                        const uint32_t k1 = G == 2 ? ((a1s[m] & 0xFFu) + 32768u - 128u) : a16;
                         const int i1 = (int)k1 - 32768 + J.dense_b1;
                         const int i2 = G == 2 ? a + J.dense_b2 : 0;
                         if (i1 >= 0 && i1 <= 2 * J.dense_b1 && i2 >= 0 && i2 <= 2 * J.dense_b2)
@@ -557,9 +679,22 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
                             hist_insert(J, G == 2 ? ((unsigned long long)a16 << 16 | k1) : a16, 1u);
                     }
                 } else {
-                    const unsigned long long part = (unsigned long long)a16 << (16 * k);
-                    if (k == 0) keys[m] = part;
-                    else keys[m] |= part;
+                    // slot k: this member's final a_{k+1}; with orbits, slots of the
+                    // multiples (k+1) t collect (k+1) (E or N - Z) as int16
+                    unsigned long long key = k == 0 ? 0ull : keys[m];
+                    key = (key & ~(0xFFFFull << (16 * k))) | ((unsigned long long)a16 << (16 * k));
+                    if (orb) {
+#pragma unroll
+                        for (int t = 2; t <= G; ++t) {
+                            const int kk = (k + 1) * t - 1;
+                            if (kk >= G) break;
+                            const int add = (k + 1) * ((t & 1) ? E : Nm - Z);
+                            const int cur = k == 0 ? 0 : (int)(int16_t)(uint16_t)(key >> (16 * kk));
+                            key = (key & ~(0xFFFFull << (16 * kk))) |
+                                  ((unsigned long long)(uint16_t)(int16_t)(cur + add) << (16 * kk));
+                        }
+                    }
+                    keys[m] = key;
                 }
             }
         }

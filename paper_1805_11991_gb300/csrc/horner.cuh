@@ -46,14 +46,21 @@ __device__ __forceinline__ void dense_chain(const Tab T, const uint32_t (&dli)[D
     }
 }
 
+// sum of chi(f(x)) over this lane's share of the field's points x = alpha^j:
+// j = pts[i] for i < npts (one point per Frobenius orbit), or every j < L when
+// pts is null; zeros += the points with f(x) = 0
 template <int D, bool TRIPLE, class Tab>
 __device__ __forceinline__ int field_chi_sum(const Tab T, uint32_t L, uint32_t bar,
-                                             const uint32_t (&lam)[D + 1], uint32_t nz, int lane)
+                                             const uint32_t (&lam)[D + 1], uint32_t nz, int lane,
+                                             const uint32_t *__restrict__ pts, uint32_t npts, int &zeros)
 {
     const uint32_t cap = TRIPLE ? 3 * L : 2 * L;
     int S = 0;
-    if (nz == 0) {   // f = c_D x^D
-        for (uint32_t j = lane; j < L; j += 32) S += ((lam[D] + (uint32_t)D * j) & 1u) ? -1 : 1;
+    if (nz == 0) {   // f = c_D x^D (never 0 at x != 0)
+        for (uint32_t i = lane; i < npts; i += 32) {
+            const uint32_t j = pts ? __ldg(pts + i) : i;
+            S += ((lam[D] + (uint32_t)D * j) & 1u) ? -1 : 1;
+        }
         return S;
     }
     const int i1 = 31 - __clz(nz);
@@ -82,10 +89,14 @@ __device__ __forceinline__ int field_chi_sum(const Tab T, uint32_t L, uint32_t b
     }
     // dense patterns get a branch-free chain
     const int dense = (nz == (1u << (D - 1)) - 1u) ? 2 : (nz == (1u << D) - 1u) ? 1 : 0;
-    for (uint32_t j0 = 0; j0 < L; j0 += 64) {
-        const uint32_t jA = j0 + lane, jB = j0 + 32 + lane;
-        const bool vA = jA < L, vB = jB < L;
-        const uint32_t xA = vA ? jA : 0, xB = vB ? jB : 0;
+    for (uint32_t i0 = 0; i0 < npts; i0 += 64) {
+        const uint32_t iA = i0 + lane, iB = i0 + 32 + lane;
+        const bool vA = iA < npts, vB = iB < npts;
+        uint32_t xA = vA ? iA : 0, xB = vB ? iB : 0;
+        if (pts) {
+            xA = __ldg(pts + xA);
+            xB = __ldg(pts + xB);
+        }
         uint32_t mA, mB;
         if (g1 == 2) {   // lead at D, first nonzero at D-2: 2j mod L
             mA = min(2 * xA, 2 * xA - L);
@@ -128,6 +139,7 @@ __device__ __forceinline__ int field_chi_sum(const Tab T, uint32_t L, uint32_t b
         if (__any_sync(kFull, pA || pB)) {
             if (pA) cA = slow_chi<D>(T, L, cap, lam, nz, xA);
             if (pB) cB = slow_chi<D>(T, L, cap, lam, nz, xB);
+            zeros += (pA && cA == 0) + (pB && cB == 0);
         }
         S += (vA ? cA : 0) + (vB ? cB : 0);
     }
@@ -156,7 +168,12 @@ __device__ __forceinline__ void process_tile(const KJob &J, uint64_t tile, const
     bool sqf = false;
     if (valid) {
         const uint32_t *coef1 = s32 + J.coef_off[0];
-        if (J.tab_kind[0] != kTabDoubleGlobal) {
+        if (J.tab_kind[0] == kTab17Smem) {
+            FqLog<Tab17> F{Tab17{s16 + J.tab_off[0], reinterpret_cast<const uint32_t *>(s16 + J.tab_hi_off[0]),
+                                 J.L[0]},
+                           J.L[0]};
+            sqf = squarefree<D>(F, coef1, J.p, c);
+        } else if (J.tab_kind[0] != kTabDoubleGlobal) {
             FqLog<TabS> F{TabS{s16 + J.tab_off[0]}, J.L[0]};
             sqf = squarefree<D>(F, coef1, J.p, c);
         } else {
@@ -172,9 +189,9 @@ __device__ __forceinline__ void process_tile(const KJob &J, uint64_t tile, const
     }
     unsigned todo = J.unfiltered ? vmask : smask;
 
-    int32_t myN[G];
+    int myE[G], myZ[G];   // per field m = k+1: sum of chi and zeros over its points (x = 0 in field 1)
 #pragma unroll
-    for (int k = 0; k < G; ++k) myN[k] = 0;
+    for (int k = 0; k < G; ++k) myE[k] = myZ[k] = 0;
 
     while (todo) {
         const int src = __ffs(todo) - 1;
@@ -192,20 +209,42 @@ __device__ __forceinline__ void process_tile(const KJob &J, uint64_t tile, const
             uint32_t lam[D + 1];
 #pragma unroll
             for (int i = 0; i <= D; ++i) lam[i] = coefk[cc[i]];
-            int S;
+            int S, Zr = 0;
             const uint32_t kind = J.tab_kind[k];
+            const uint32_t *pts = J.reps[k];
+            const uint32_t np = J.npts[k];
             if (kind == kTabTripleSmem)
-                S = field_chi_sum<D, true>(TabS{s16 + J.tab_off[k]}, L, J.barrett[k], lam, nz, lane);
+                S = field_chi_sum<D, true>(TabS{s16 + J.tab_off[k]}, L, J.barrett[k], lam, nz, lane, pts, np, Zr);
             else if (kind == kTabDoubleSmem)
-                S = field_chi_sum<D, false>(TabS{s16 + J.tab_off[k]}, L, J.barrett[k], lam, nz, lane);
+                S = field_chi_sum<D, false>(TabS{s16 + J.tab_off[k]}, L, J.barrett[k], lam, nz, lane, pts, np, Zr);
+            else if (kind == kTab17Smem)
+                S = field_chi_sum<D, false>(
+                    Tab17{s16 + J.tab_off[k], reinterpret_cast<const uint32_t *>(s16 + J.tab_hi_off[k]), L}, L,
+                    J.barrett[k], lam, nz, lane, pts, np, Zr);
             else
-                S = field_chi_sum<D, false>(TabG{J.zech2w[k]}, L, J.barrett[k], lam, nz, lane);
-            if (lane == 0 && cc[0] != 0) S += (lam[0] & 1u) ? -1 : 1;   // x = 0
+                S = field_chi_sum<D, false>(TabG{J.zech2w[k]}, L, J.barrett[k], lam, nz, lane, pts, np, Zr);
+            if (lane == 0 && !pts) {   // x = 0 (in F_q; in every field when every point is evaluated)
+                if (cc[0] != 0) S += (lam[0] & 1u) ? -1 : 1;
+                else Zr += 1;
+            }
             S = __reduce_add_sync(kFull, S);
-            // points at infinity: 1 + chi(c_{2g+2})
+            Zr = __reduce_add_sync(kFull, Zr);
+            if (lane == src) {
+                myE[k] = S;
+                myZ[k] = Zr;
+            }
+        }
+    }
+    // #C_k = Q_k + S_k + 1 + chi(c_{2g+2})  (points at infinity; chi of c_d in F_{q^k})
+    int32_t myN[G];
+    {
+        int Sk[G];
+        orbit_combine<G>(J, myE, myZ, Sk);
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
             int inf = 1;
-            if (D == 2 * G + 2) inf += (lam[D] & 1u) ? -1 : 1;
-            if (lane == src) myN[k] = (int32_t)J.Q[k] + S + inf;
+            if (D == 2 * G + 2) inf += (s32[J.coef_off[k] + c[D]] & 1u) ? -1 : 1;
+            myN[k] = (int32_t)J.Q[k] + Sk[k] + inf;
         }
     }
 
@@ -218,10 +257,44 @@ __device__ __forceinline__ void process_tile(const KJob &J, uint64_t tile, const
         return;
     }
     unsigned long long key = 0;
+    if (J.lam_mode) {
+        // (a_1..a_g, lambda(f)) of eq. 1.2: the orbit zeros of exact degree m are
+        // the irreducible factors of degree m; what is left is one factor, or two
+        // of degree g+1 when chi(disc f) = +1 (Stickelberger)
+        uint32_t used = 0;
+        unsigned long long lam = 0;
 #pragma unroll
-    for (int k = 0; k < G; ++k) {
-        const int a = (int)J.Q[k] + 1 - myN[k];   // eq. 1.1
-        key |= (unsigned long long)((uint32_t)(a + 32768) & 0xFFFFu) << (16 * k);
+        for (int m = 1; m <= G; ++m) {
+            const uint32_t nm = (uint32_t)myZ[m - 1];
+            lam |= (unsigned long long)(nm & 0xFu) << (4 * (m - 1));
+            used += (uint32_t)m * nm;
+        }
+        if (sqf && D == 2 * G + 2 && used == 0) {
+            int dc;
+            const uint32_t *coef1 = s32 + J.coef_off[0];
+            if (J.tab_kind[0] == kTab17Smem)
+                dc = disc_chi<D>(FqLog<Tab17>{Tab17{s16 + J.tab_off[0],
+                                                    reinterpret_cast<const uint32_t *>(s16 + J.tab_hi_off[0]), J.L[0]},
+                                              J.L[0]},
+                                 coef1, J.p, J.q, c);
+            else if (J.tab_kind[0] != kTabDoubleGlobal)
+                dc = disc_chi<D>(FqLog<TabS>{TabS{s16 + J.tab_off[0]}, J.L[0]}, coef1, J.p, J.q, c);
+            else
+                dc = disc_chi<D>(FqLog<TabG>{TabG{J.zech2w[0]}, J.L[0]}, coef1, J.p, J.q, c);
+            if (dc > 0) lam |= 1ull << (4 * G);
+        }
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            const int a = (int)J.Q[k] + 1 - myN[k];   // eq. 1.1
+            key |= (unsigned long long)(uint32_t)(a + J.key_bias[k]) << J.key_shift[k];
+        }
+        key |= lam << J.lam_shift;
+    } else {
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            const int a = (int)J.Q[k] + 1 - myN[k];   // eq. 1.1
+            key |= (unsigned long long)((uint32_t)(a + 32768) & 0xFFFFu) << (16 * k);
+        }
     }
     if (sqf) {
         const unsigned peers = __match_any_sync(smask, key);
@@ -235,10 +308,9 @@ __device__ __forceinline__ void process_tile(const KJob &J, uint64_t tile, const
 // Persistent: CTAs pull work items (a run of tiles of one job) from a counter
 // until the queue is empty; a CTA restages tables only when its job changes.
 template <int D>
-__global__ void __launch_bounds__(256) k_persistent(const KJob *__restrict__ jobs,
-                                                    const uint64_t *__restrict__ item_start,
-                                                    uint32_t n_jobs, uint64_t n_items,
-                                                    unsigned long long *counter, uint32_t item_tiles)
+__device__ __forceinline__ void persistent_body(const KJob *__restrict__ jobs, const uint64_t *__restrict__ item_start,
+                                                uint32_t n_jobs, uint64_t n_items, unsigned long long *counter,
+                                                uint32_t item_tiles)
 {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ unsigned long long s_item;
@@ -274,6 +346,29 @@ __global__ void __launch_bounds__(256) k_persistent(const KJob *__restrict__ job
     if (cur >= 0) flush_stats(jobs[cur], st, lane);
 }
 
+// up to 256 threads (several CTAs per SM)
+template <int D>
+__global__ void __launch_bounds__(256) k_persistent(const KJob *__restrict__ jobs,
+                                                    const uint64_t *__restrict__ item_start, uint32_t n_jobs,
+                                                    uint64_t n_items, unsigned long long *counter,
+                                                    uint32_t item_tiles)
+{
+    persistent_body<D>(jobs, item_start, n_jobs, n_items, counter, item_tiles);
+}
+
+// up to 768 threads (512 for degrees >= 7, whose longer chains need more than
+// 80 registers): for jobs whose tables leave room for one CTA per SM (the
+// 17-bit Zech table of F_{293^2}, the u16 table of F_{13^4}), which then still
+// keep 16-24 warps resident
+template <int D>
+__global__ void __launch_bounds__(D <= 6 ? 768 : 512, 1) k_persistent_wide(const KJob *__restrict__ jobs,
+                                                            const uint64_t *__restrict__ item_start,
+                                                            uint32_t n_jobs, uint64_t n_items,
+                                                            unsigned long long *counter, uint32_t item_tiles)
+{
+    persistent_body<D>(jobs, item_start, n_jobs, n_items, counter, item_tiles);
+}
+
 template <int D>
 __global__ void __launch_bounds__(256) k_na_count(const KJob J)
 {
@@ -291,6 +386,7 @@ template <int D>
 const void *horner_pick(int which)
 {
     if (which == 1) return (const void *)k_persistent<D>;
+    if (which == 3) return (const void *)k_persistent_wide<D>;
     if (which == 0) return nullptr;   // plain runs use the persistent kernel, one job per launch
     return (const void *)k_na_count<D>;
 }

@@ -56,6 +56,12 @@ struct Tables {
     // a step index z + d + j with z, d, j < L needs no reduction.  u16 when
     // 3L < 65536.
     uint16_t *d_zech3 = nullptr;    // [3L+1] or null
+    // 17-bit layout for fields too large for u16 entries (2L >= 65536, L < 2^17 - 1):
+    // entry u in [0, L] is lo[u] | (bit u of hi) << 16; Z[u] for u < L, and the
+    // marker 0x1FFFF at u = L/2 (1 + alpha^u = 0) and at u = L (the poison of the
+    // doubled index range folded back by one subtraction of L)
+    uint16_t *d_z17lo = nullptr;    // [L+1] or null
+    uint32_t *d_z17hi = nullptr;    // [(L+32)/32] or null
     // Fan-out rows (q <= 63): bit c of row l is 1 iff chi(alpha^l + c) = -1 for
     // the F_q digit c; the top bit (31 or 63) marks rows with alpha^l in F_q^x,
     // where alpha^l + c = 0 for the digit c = zdig[l / (L/(q-1))].
@@ -70,6 +76,11 @@ struct Tables {
     // for alpha^l = e_y0 + e_y1 alpha: bits 0-7 -y0, bits 8-15 -y1; bits 16-23
     // 1/y1 and bits 24-31 -y0/y1 when y1 != 0, else 0 and -y0 (digits)
     uint32_t *d_coord2 = nullptr;   // [L]
+    // Frobenius orbits (k >= 2): the logs j of one element alpha^j per orbit
+    // {x, x^q, ..., x^(q^(k-1))} of the elements of exact degree k over F_q
+    // (the smallest j of the orbit), ascending; n_reps of them
+    uint32_t *d_reps = nullptr;     // [n_reps] or null (k = 1)
+    uint32_t n_reps = 0;
 };
 
 // where a count kernel reads the Zech table of one field
@@ -77,9 +88,12 @@ enum TabKind : uint32_t {
     kTabTripleSmem = 0,   // d_zech3 staged in shared memory
     kTabDoubleSmem = 1,   // d_zech2 staged in shared memory
     kTabDoubleGlobal = 2, // d_zech2w read from global memory (L1/L2)
+    kTab17Smem = 3,       // d_z17lo / d_z17hi staged in shared memory (per-member kernel)
 };
 
 int tables_build(uint32_t q, uint32_t k, Tables **out);
+// one point per Frobenius orbit of the elements of exact degree k (host)
+std::vector<uint32_t> orbit_reps(uint32_t q, uint32_t k, uint32_t L);
 void tables_destroy(Tables *t);
 // process-wide cache of tables per (device, q, k); never freed before exit
 int tables_cached(uint32_t q, uint32_t k, const Tables **out);
@@ -106,6 +120,22 @@ struct KJob {
     const uint16_t *zech2[kMaxG];
     const uint32_t *zech2w[kMaxG];
     const uint32_t *coef_log[kMaxG];
+    const uint16_t *z17lo[kMaxG];     // 17-bit layout (Tables::d_z17lo / d_z17hi) or null
+    const uint32_t *z17hi[kMaxG];
+    uint32_t tab_hi_off[kMaxG];       // kTab17Smem: u16 offset of the high-bit plane in smem
+    // points evaluated in field m = k+1: one per Frobenius orbit of the
+    // elements of exact degree m (reps[k], npts[k] of them), or every point of
+    // F_Q^x (reps[k] null, npts[k] = L); field 1 always takes every point
+    const uint32_t *reps[kMaxG];
+    uint32_t npts[kMaxG];
+    uint32_t zshift[kMaxG];           // two-level kernel: zeros ride in bits zshift.. of its
+                                      // accumulators (0: field's zeros not needed apart)
+    // HWC_FLAG_LAMBDA (per-member kernel): key = sum_k (a_k + key_bias[k]) << key_shift[k]
+    // | (n_1..n_g in 4 bits each, then one bit: two factors of degree g+1) << lam_shift
+    uint32_t lam_mode;
+    uint32_t key_shift[kMaxG];
+    int32_t key_bias[kMaxG];
+    uint32_t lam_shift;
     uint32_t smem_u16;                // u16 words of zech2 tables staged in smem
     uint32_t smem_bytes;              // total dynamic smem for this job
     // c_0 fan-out (method 1): groups of q members that differ only in c_0
@@ -170,6 +200,9 @@ struct TuneChoice {
     bool no_triple = false;   // shared Zech tables in the doubled layout only
 };
 bool layout_job_smem(KJob &j, uint32_t smem_limit, bool no_triple = false);
+// the points field k (1-based) evaluates: one per Frobenius orbit (orbits,
+// k >= 2) or all of F_Q^x; and the two-level kernel's zero shift
+void set_points(KJob &kj, uint32_t k, const Tables *t, bool orbits);
 // validates a job and fills a KJob (tables, method, layout); outputs left null
 int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n, uint32_t flags, const TuneChoice *tc = nullptr);
 // autotuner: the fastest measured choice for the job's class (measured on a
@@ -181,7 +214,8 @@ bool tune_lookup(const hwc_job_t &jb, uint32_t flags, TuneChoice *out);
 int batch_create_with(const hwc_job_t *jobs, size_t n, uint32_t flags, const TuneChoice *tc, hwc_batch **out);
 // launch shape for a kernel (degree, method, row words) at this much dynamic smem
 int choose_shape(int D, uint32_t method, uint32_t words, uint32_t smem, bool persistent, LaunchShape *out);
-// kernel entry points by degree: which = 1 persistent, 2 allocation-free
+// kernel entry points by degree: which = 1 persistent (<= 256 threads),
+// 2 allocation-free, 3 persistent with up to 768 threads
 const void *horner_kernel(int D, int which);
 const void *horner_kernel_a(int D, int which);   // horner_a.cu, D = 3..6
 const void *horner_kernel_b(int D, int which);   // horner_b.cu, D = 7, 8
@@ -202,6 +236,7 @@ constexpr int kFan2WarpsHost = 4;   // warps per CTA of the two-level kernel
 // lanes per value of c_1; offsets in bytes):
 //   U[us] u32: staged log u(x) for 64 points; us = 96 when 64/S is not a
 //              multiple of 8 (the lanes' 8-point blocks overrun 64), else 64
+//   Dd[us] u32: staged log u(x) - log x (orbit points)
 //   acc[32][q] u16: per-lane rows of 2 cnt + z for every c_0 (lane s q + b
 //              holds (c_1 = b, chunk s); lanes past S q fill unused rows)
 //   rq[16][32] u16: per-lane queue of row indices with a zero digit
@@ -216,14 +251,15 @@ constexpr uint32_t kFan2Queue = 16;
 constexpr uint32_t kFan2Prefix = 64;
 constexpr uint32_t kFan2ZeroRow = 8;   // row index L + 8
 struct Fan2Layout {
-    uint32_t us, acc_off, rq_off, sqf_off, par_off, a1_off, bytes;
+    uint32_t us, ds_off, acc_off, rq_off, sqf_off, par_off, a1_off, bytes;
 };
 __host__ __device__ inline Fan2Layout fan2_layout(uint32_t q, bool dense)
 {
     Fan2Layout l;
     const uint32_t S = 32 / q, nw = (q * q + 31) / 32;
     l.us = (S == 1 || S == 2 || S == 4 || S == 8) ? 64 : 96;
-    l.acc_off = 4 * l.us;
+    l.ds_off = 4 * l.us;
+    l.acc_off = 8 * l.us;
     l.rq_off = l.acc_off + ((64 * q + 3) & ~3u);
     l.sqf_off = l.rq_off + 2 * kFan2Queue * 32;
     l.par_off = (l.sqf_off + 4 * nw + 15) & ~15u;
@@ -252,8 +288,10 @@ struct hwc_tables {
 
 struct hwc_hist {
     uint32_t g = 0;
-    std::vector<int32_t> counts;   // n * g, lexicographically sorted
+    std::vector<int32_t> counts;   // n * g, lexicographically sorted (after lam)
     std::vector<uint64_t> mult;
+    std::vector<uint64_t> lam;     // factorisation pattern codes (HWC_FLAG_LAMBDA), else empty
+    bool has_lam = false;
     uint64_t n_total = 0, n_sqf = 0;
 };
 

@@ -107,8 +107,13 @@ static uint64_t isqrt_u64(uint64_t v)   // floor(sqrt(v))
 bool layout_job_smem(KJob &j, uint32_t smem_limit, bool no_triple)
 {
     uint32_t kind[kMaxG];
+    // the per-member kernel can also read a 17-bit table from shared memory
+    auto small17 = [&](uint32_t k) { return j.method == 0 && j.z17lo[k] && j.z17hi[k]; };
     for (uint32_t k = 0; k < j.g; ++k)
-        kind[k] = (j.zech3[k] && !no_triple) ? kTabTripleSmem : (j.zech2[k] ? kTabDoubleSmem : kTabDoubleGlobal);
+        kind[k] = (j.zech3[k] && !no_triple) ? kTabTripleSmem
+                  : j.zech2[k]              ? kTabDoubleSmem
+                  : small17(k)              ? kTab17Smem
+                                            : kTabDoubleGlobal;
     // the two-level kernel's lanes b read Zech entries log b apart: multiples
     // of s = L/(q-1).  For s = 0 mod 4 those fall on few banks unless the
     // table carries one pad word per 32.
@@ -118,8 +123,9 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit, bool no_triple)
         uint64_t n = 0;
         if (kind[k] == kTabTripleSmem) n = 3ull * j.L[k] + 1;
         else if (kind[k] == kTabDoubleSmem) n = 2ull * j.L[k] + 1;
+        else if (kind[k] == kTab17Smem) return (((j.L[k] + 2ull) & ~1ull) + 2 * ((j.L[k] + 32ull) / 32) + 7) / 8 * 8;
         else return 0;
-        if (j.method == 2) n += kFan2Prefix;
+        if (j.method == 2) n += kFan2Prefix;   // (method 2 never takes the 17-bit layout)
         if (pad[k]) n += 2 * ((n + 63) / 64);
         return ((n + 7) / 8) * 8;
     };
@@ -157,7 +163,9 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit, bool no_triple)
         for (uint32_t k = 0; k < j.g; ++k)
             if (kind[k] != kTabDoubleGlobal && (big < 0 || words(k) > words(big))) big = (int)k;
         if (big < 0) break;
-        kind[big] = (kind[big] == kTabTripleSmem && j.zech2[big]) ? kTabDoubleSmem : kTabDoubleGlobal;
+        kind[big] = (kind[big] == kTabTripleSmem && j.zech2[big]) ? kTabDoubleSmem
+                    : (kind[big] != kTab17Smem && small17(big)) ? kTab17Smem
+                                                                 : kTabDoubleGlobal;
     }
     if (bytes_for() > smem_limit) return false;
     if (j.method == 2)   // the two-level kernel reads every Zech table from shared memory
@@ -166,8 +174,10 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit, bool no_triple)
     uint32_t off = 0;
     for (uint32_t k = 0; k < kMaxG; ++k) {
         j.tab_kind[k] = k < j.g ? kind[k] : kTabDoubleGlobal;
-        j.tab_pad[k] = (k < j.g && kind[k] != kTabDoubleGlobal) ? pad[k] : 0u;
+        j.tab_pad[k] = (k < j.g && kind[k] != kTabDoubleGlobal && kind[k] != kTab17Smem) ? pad[k] : 0u;
         j.tab_off[k] = off;
+        // 17-bit layout: L + 1 low halves (even count), then the high-bit plane
+        j.tab_hi_off[k] = off + (k < j.g ? ((j.L[k] + 2u) & ~1u) : 0u);
         if (k < j.g) off += (uint32_t)words(k);
     }
     j.smem_u16 = off;
@@ -250,6 +260,22 @@ struct HostJob {
     int warps = 0;   // tuned warps per CTA (two-level kernel)
 };
 
+void set_points(KJob &kj, uint32_t k, const Tables *t, bool orbits)
+{
+    const bool orb = orbits && k >= 2 && t->d_reps;
+    kj.reps[k - 1] = orb ? t->d_reps : nullptr;
+    kj.npts[k - 1] = orb ? t->n_reps : t->L;
+    // the two-level kernel keeps the zeros of field m apart when some
+    // S_k = ... + m (N_m - Z_m) needs them (k = 2m, 4m <= g): in bits s.. of
+    // its accumulators, 2^s above 2 (points) + (zeros <= d)
+    kj.zshift[k - 1] = 0;
+    if (orbits && 2 * k <= kj.g) {
+        uint32_t s = 0;
+        while ((1u << s) <= 2 * kj.npts[k - 1] + kj.d) ++s;
+        kj.zshift[k - 1] = s;
+    }
+}
+
 int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n, uint32_t flags, const TuneChoice *tc)
 {
     int rc = validate_job(jb, fam_n);
@@ -268,8 +294,27 @@ int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n, uint32_t flags, co
     upow(jb.q, kj.d - 1, &kj.fam_mz);
     kj.qd = kj.fam_mz * jb.q;
     kj.n_tiles = (jb.count + kTileMembers - 1) / kTileMembers;
+    if ((flags & HWC_FLAG_LAMBDA) && (flags & HWC_FLAG_ALL_POINTS))
+        return set_error(HWC_ERR_ARG, "HWC_FLAG_LAMBDA needs the Frobenius-orbit points (not HWC_FLAG_ALL_POINTS)");
+    if (flags & HWC_FLAG_LAMBDA) {
+        // key: a_k + B_k in just enough bits per field, then n_1..n_g and the split bit
+        kj.lam_mode = 1;
+        uint32_t off = 0;
+        double Qk = 1;
+        for (uint32_t k = 0; k < jb.g; ++k) {
+            Qk *= jb.q;
+            const int32_t B = (int32_t)std::floor(2.0 * jb.g * std::sqrt(Qk));
+            uint32_t w = 0;
+            while ((1ull << w) <= 2ull * (uint64_t)B) ++w;
+            kj.key_bias[k] = B;
+            kj.key_shift[k] = off;
+            off += w;
+        }
+        kj.lam_shift = off;
+        if (off + 4 * jb.g + 1 > 63) return set_error(HWC_ERR_TOO_LARGE, "lambda key needs %u bits", off + 4 * jb.g + 1);
+    }
     // enumerated families with q <= 63: groups of q members share all but c_0
-    const bool fan = !(flags & HWC_FLAG_HORNER) && jb.family.kind != HWC_FAM_MONIC_NOSUB_SAMPLED && jb.q <= 63 &&
+    const bool fan = !(flags & (HWC_FLAG_HORNER | HWC_FLAG_LAMBDA)) && jb.family.kind != HWC_FAM_MONIC_NOSUB_SAMPLED && jb.q <= 63 &&
                      !(tc && tc->method == 0);
     const bool no_triple = tc && tc->no_triple;
     // (method chosen below: two-level fan-out for q <= 31, one-level up to 63,
@@ -285,6 +330,9 @@ int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n, uint32_t flags, co
         kj.zech3[k - 1] = t->d_zech3;
         kj.zech2w[k - 1] = t->d_zech2w;
         kj.coef_log[k - 1] = t->d_coef_log;
+        kj.z17lo[k - 1] = t->d_z17lo;
+        kj.z17hi[k - 1] = t->d_z17hi;
+        set_points(kj, k, t, !(flags & HWC_FLAG_ALL_POINTS));
         kj.rows[k - 1] = jb.q <= 31 ? (const void *)t->d_rows32 : (const void *)t->d_rows64;
         if (k == 1) {
             kj.fq_mul = t->d_fq_mul;
@@ -336,47 +384,90 @@ using namespace hwc;
 // ---------------------------------------------------------------------
 // histograms
 
-static hwc_hist *hist_from_map(uint32_t g, const std::map<std::vector<int32_t>, uint64_t> &m,
-                               uint64_t n_total)
+// entries keyed by (pattern code, tuple); without patterns the code is 0
+using HistMap = std::map<std::pair<uint64_t, std::vector<int32_t>>, uint64_t>;
+
+static hwc_hist *hist_from_map(uint32_t g, const HistMap &m, uint64_t n_total, bool has_lam)
 {
     hwc_hist *h = new hwc_hist();
     h->g = g;
     h->n_total = n_total;
+    h->has_lam = has_lam;
     h->counts.reserve(m.size() * g);
     h->mult.reserve(m.size());
     for (auto &kv : m) {
-        h->counts.insert(h->counts.end(), kv.first.begin(), kv.first.end());
+        h->counts.insert(h->counts.end(), kv.first.second.begin(), kv.first.second.end());
+        if (has_lam) h->lam.push_back(kv.first.first);
         h->mult.push_back(kv.second);
         h->n_sqf += kv.second;
     }
     return h;
 }
 
+// the full pattern code of eq. 1.2 from a lambda-mode key: n_1..n_g, the
+// degree left over (one factor, or two of degree g+1 with the split bit) and
+// the extra part 1 of odd degree
+static uint64_t lambda_code(const KJob &kj, uint64_t key)
+{
+    const uint32_t g = kj.g, d = kj.d;
+    uint32_t n[2 * kMaxG + 3] = {};
+    uint32_t used = 0;
+    for (uint32_t m = 1; m <= g; ++m) {
+        n[m] = (uint32_t)(key >> (kj.lam_shift + 4 * (m - 1))) & 0xFu;
+        used += m * n[m];
+    }
+    const bool split = (key >> (kj.lam_shift + 4 * g)) & 1u;
+    if (used < d) {
+        if (split) n[g + 1] += 2;
+        else n[d - used] += 1;
+    }
+    if (d == 2 * g + 1) n[1] += 1;
+    uint64_t code = 0;
+    for (uint32_t m = 1; m <= 2 * g + 2; ++m) code += (uint64_t)n[m] << (4 * (m - 1));
+    return code;
+}
+
 hwc_hist *hwc::hist_from_keys(const KJob &kj, const unsigned long long *keys,
                               const unsigned long long *cnt, uint64_t n, uint64_t n_total)
 {
-    const uint32_t g = kj.g;
-    std::vector<uint64_t> order(n);
-    std::vector<int32_t> tup(n * g);
-    for (uint64_t i = 0; i < n; ++i) {
-        for (uint32_t k = 0; k < g; ++k) {
-            int a = (int)((keys[i] >> (16 * k)) & 0xFFFFu) - 32768;
-            tup[i * g + k] = (int32_t)kj.Q[k] + 1 - a;   // #C = Q + 1 - a (eq. 1.1)
+    if (kj.lam_mode) {   // (a_1..a_g, lambda) keys: decode, then sort by (pattern, tuple)
+        HistMap m;
+        for (uint64_t i = 0; i < n; ++i) {
+            std::vector<int32_t> t(kj.g);
+            for (uint32_t k = 0; k < kj.g; ++k) {
+                const uint32_t w = (k + 1 < kj.g ? kj.key_shift[k + 1] : kj.lam_shift) - kj.key_shift[k];
+                const int a = (int)((keys[i] >> kj.key_shift[k]) & ((1ull << w) - 1)) - kj.key_bias[k];
+                t[k] = (int32_t)kj.Q[k] + 1 - a;   // #C = Q + 1 - a (eq. 1.1)
+            }
+            m[{lambda_code(kj, keys[i]), t}] += cnt[i];
         }
+        return hist_from_map(kj.g, m, n_total, true);
     }
-    std::iota(order.begin(), order.end(), 0);
-    std::sort(order.begin(), order.end(), [&](uint64_t x, uint64_t y) {
-        return std::lexicographical_compare(&tup[x * g], &tup[x * g] + g, &tup[y * g], &tup[y * g] + g);
-    });
+    // #C_k = Q_k + 1 - a_k (eq. 1.1) and key slot k holds a_k + 32768, so the
+    // tuples in lexicographic order of (#C_1, ..., #C_g) are the keys in
+    // ascending order of sum_k (0xFFFF - slot_k) 2^(16 (g-1-k)): one sort of
+    // 64-bit words
+    const uint32_t g = kj.g;
+    std::vector<std::pair<uint64_t, uint64_t>> ord(n);
+    for (uint64_t i = 0; i < n; ++i) {
+        uint64_t t = 0;
+        for (uint32_t k = 0; k < g; ++k) t = (t << 16) | (0xFFFFu - ((keys[i] >> (16 * k)) & 0xFFFFu));
+        ord[i] = {t, cnt[i]};
+    }
+    std::sort(ord.begin(), ord.end());
     hwc_hist *h = new hwc_hist();
     h->g = g;
     h->n_total = n_total;
     h->counts.resize(n * g);
     h->mult.resize(n);
     for (uint64_t i = 0; i < n; ++i) {
-        std::copy(&tup[order[i] * g], &tup[order[i] * g] + g, &h->counts[i * g]);
-        h->mult[i] = cnt[order[i]];
-        h->n_sqf += cnt[order[i]];
+        const uint64_t t = ord[i].first;
+        for (uint32_t k = 0; k < g; ++k) {
+            const int a = (int)(0xFFFFu - ((t >> (16 * (g - 1 - k))) & 0xFFFFu)) - 32768;
+            h->counts[i * g + k] = (int32_t)kj.Q[k] + 1 - a;
+        }
+        h->mult[i] = ord[i].second;
+        h->n_sqf += ord[i].second;
     }
     return h;
 }
@@ -418,6 +509,12 @@ struct hwc_batch {
     uint64_t d2h_last = 0;
     int device = 0;
     uint32_t launches_per_run = 0;
+    // persistent batches with several launch groups: the groups after the
+    // first run on side streams (forked from and joined to the launch
+    // stream), so the tail of one launch overlaps the others
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> side_done;
+    cudaEvent_t fork = nullptr;
 };
 
 static void batch_release(hwc_batch *b)
@@ -430,6 +527,9 @@ static void batch_release(hwc_batch *b)
     if (b->t1) cudaEventDestroy(b->t1);
     if (b->h_jobs) cudaFreeHost(b->h_jobs);
     if (b->h_item_start) cudaFreeHost(b->h_item_start);
+    for (cudaStream_t st : b->side) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : b->side_done) cudaEventDestroy(ev);
+    if (b->fork) cudaEventDestroy(b->fork);
     for (void *p : b->allocs) cudaFree(p);
     delete b;
 }
@@ -460,12 +560,22 @@ static int batch_enqueue(hwc_batch *b, cudaStream_t s, bool capturing)
     // inside a graph capture an event record must be an external node to time anything
     if (b->t0) HWC_CUDA_TRY(capturing ? cudaEventRecordWithFlags(b->t0, s, cudaEventRecordExternal)
                                       : cudaEventRecord(b->t0, s));
+    const bool fork = !b->side.empty();
+    if (fork) HWC_CUDA_TRY(cudaEventRecord(b->fork, s));
     for (size_t g = 0; g < b->groups.size(); ++g) {
         const BatchGroup &G = b->groups[g];
+        cudaStream_t gs = s;
+        if (fork && g > 0) {
+            gs = b->side[g - 1];
+            HWC_CUDA_TRY(cudaStreamWaitEvent(gs, b->fork, 0));
+        }
         rc = launch_persistent(G.D, G.method, G.words, b->d_jobs + G.first, b->d_item_start + G.start_off, G.n,
-                               G.n_items, b->d_counters + g, G.max_smem, G.shape, s);
+                               G.n_items, b->d_counters + g, G.max_smem, G.shape, gs);
         if (rc) return rc;
+        if (fork && g > 0) HWC_CUDA_TRY(cudaEventRecord(b->side_done[g - 1], gs));
     }
+    if (fork)
+        for (cudaEvent_t ev : b->side_done) HWC_CUDA_TRY(cudaStreamWaitEvent(s, ev, 0));
     if (b->t1) HWC_CUDA_TRY(capturing ? cudaEventRecordWithFlags(b->t1, s, cudaEventRecordExternal)
                                       : cudaEventRecord(b->t1, s));
     return launch_compact(b->d_jobs, nj, s);
@@ -476,8 +586,10 @@ int hwc::choose_shape(int D, uint32_t method, uint32_t words, uint32_t smem, boo
 {
     const int sms = device_sm_count();
     int best_block = 256, best_warps = -1, best_ctas = 1;
-    const int blocks[2] = {method == 2 ? kFan2WarpsHost * 32 : 256, 128};
-    for (int bi = 0; bi < (method == 0 ? 2 : 1); ++bi) {
+    // per-member kernel: 256 threads unless only a larger block keeps more
+    // warps resident (one CTA per SM for the 17-bit tables)
+    const int blocks[4] = {method == 2 ? kFan2WarpsHost * 32 : 256, 128, 512, 768};
+    for (int bi = 0; bi < (method == 0 ? 4 : 1); ++bi) {
         const int block = blocks[bi];
         int ctas = 0;
         int rc = max_ctas_per_sm(D, method, words, block, smem, persistent, &ctas);
@@ -562,7 +674,20 @@ static int batch_create_impl(const hwc_job_t *jobs, size_t n, uint32_t flags, ui
         const KJob &k = filled[x].kj;
         return std::make_tuple(k.d, k.method, k.words);
     };
-    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return gkey(x) < gkey(y); });
+    // within a launch the queue hands out the jobs' work items in this order:
+    // the costliest items first (point evaluations per tile), so that the
+    // cheap ones fill the tail of the launch
+    auto item_cost = [&](size_t x) {
+        const KJob &k = filled[x].kj;
+        double pts = 0;
+        for (uint32_t i = 0; i < k.g; ++i) pts += k.npts[i] + 1.0;
+        const double members = k.method == 2 ? (double)k.q * k.q : k.method == 1 ? (double)k.q : (double)kTileMembers;
+        return members * pts;
+    };
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) {
+        if (gkey(x) != gkey(y)) return gkey(x) < gkey(y);
+        return item_cost(x) > item_cost(y);
+    });
     b->pos.resize(n);
     b->jobs.resize(n);
     for (size_t r = 0; r < n; ++r) {
@@ -658,6 +783,21 @@ static int batch_create_impl(const hwc_job_t *jobs, size_t n, uint32_t flags, ui
         }
     }
     b->launches_per_run = 2 + (uint32_t)b->groups.size();
+    if (!(flags & HWC_FLAG_PLAIN) && b->groups.size() > 1) {   // plain runs stay one launch after another
+        bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+        for (size_t g = 1; ok && g < b->groups.size(); ++g) {
+            cudaStream_t st = nullptr;
+            cudaEvent_t ev = nullptr;
+            ok = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
+            if (ok) b->side.push_back(st);
+            ok = ok && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+            if (ok) b->side_done.push_back(ev);
+        }
+        if (!ok) {
+            batch_release(b);
+            return set_error(HWC_ERR_CUDA, "side streams of the batch could not be created");
+        }
+    }
     if (cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess) {
         batch_release(b);
         return set_error(HWC_ERR_CUDA, "cudaEventCreate failed");
@@ -850,7 +990,7 @@ extern "C" int hwc_count_members(uint32_t g, uint32_t q, const hwc_family_t *fam
     rc = prepare_count_kernels();
     if (rc) return rc;
     KJob kj;
-    rc = fill_kjob(j, kj, &fam_n, flags & (HWC_FLAG_HORNER | HWC_FLAG_FAN1));
+    rc = fill_kjob(j, kj, &fam_n, flags & (HWC_FLAG_HORNER | HWC_FLAG_FAN1 | HWC_FLAG_ALL_POINTS));
     if (rc) return rc;
     if (count == 0) return HWC_OK;
     kj.unfiltered = unfiltered ? 1u : 0u;
@@ -933,12 +1073,15 @@ extern "C" int hwc_hist_merge(hwc_hist_t *into, const hwc_hist_t *from)
 {
     if (!into || !from) return set_error(HWC_ERR_ARG, "histogram is NULL");
     if (into->g != from->g) return set_error(HWC_ERR_ARG, "genus mismatch %u vs %u", into->g, from->g);
+    if (into->has_lam != from->has_lam)
+        return set_error(HWC_ERR_ARG, "one histogram has factorisation patterns, the other not");
     const uint32_t g = into->g;
-    std::map<std::vector<int32_t>, uint64_t> m;
+    HistMap m;
     for (const hwc_hist *h : {(const hwc_hist *)into, from})
         for (size_t i = 0; i < h->mult.size(); ++i)
-            m[std::vector<int32_t>(&h->counts[i * g], &h->counts[i * g] + g)] += h->mult[i];
-    hwc_hist *r = hist_from_map(g, m, into->n_total + from->n_total);
+            m[{h->has_lam ? h->lam[i] : 0ull, std::vector<int32_t>(&h->counts[i * g], &h->counts[i * g] + g)}] +=
+                h->mult[i];
+    hwc_hist *r = hist_from_map(g, m, into->n_total + from->n_total, into->has_lam);
     std::swap(*into, *r);
     delete r;
     return HWC_OK;
@@ -949,10 +1092,18 @@ extern "C" int hwc_hist_from_arrays(uint32_t g, uint64_t n_entries, const int32_
 {
     if (!out || (n_entries && (!counts || !mult)) || g < 1 || g > (uint32_t)kMaxG)
         return set_error(HWC_ERR_ARG, "bad argument");
-    std::map<std::vector<int32_t>, uint64_t> m;
+    HistMap m;
     for (uint64_t i = 0; i < n_entries; ++i)
-        m[std::vector<int32_t>(counts + i * g, counts + i * g + g)] += mult[i];
-    *out = hist_from_map(g, m, n_total);
+        m[{0ull, std::vector<int32_t>(counts + i * g, counts + i * g + g)}] += mult[i];
+    *out = hist_from_map(g, m, n_total, false);
+    return HWC_OK;
+}
+
+extern "C" int hwc_hist_lambda(const hwc_hist_t *h, uint64_t *codes)
+{
+    if (!h) return set_error(HWC_ERR_ARG, "histogram is NULL");
+    if (!h->has_lam) return set_error(HWC_ERR_STATE, "histogram counted without HWC_FLAG_LAMBDA");
+    if (codes && !h->lam.empty()) std::memcpy(codes, h->lam.data(), h->lam.size() * sizeof(uint64_t));
     return HWC_OK;
 }
 

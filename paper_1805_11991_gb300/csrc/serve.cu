@@ -1,15 +1,19 @@
 // serve.cu -- request loop with continuous batching.
 //
-// A server thread owns a CUDA stream and runs the device in steps.  Each step
-// is one launch of the persistent count kernel over a slice of every active
-// request (an equal share of point evaluations each, about kStepMs of device
-// time in all at the rate measured on earlier steps), so requests of very
-// different sizes progress together and a request that arrives while others
-// run joins at the next step boundary once a slot and enough device memory
-// are free.  Field
-// tables stay resident in the process-wide table cache.  Each request owns its
-// histogram hash; slices of one request add into it across steps, and when
-// its last slice is done the hash is compacted and copied out.  Results do not
+// A server thread owns two CUDA streams and runs the device in steps.  Each
+// step is one launch of the persistent count kernel per kernel group over a
+// slice of every active request (an equal share of point evaluations each,
+// about kStepMs of device time in all at the rate measured on earlier steps),
+// so requests of very different sizes progress together, and a request that
+// arrives while others run joins at the next step once a slot and enough
+// device memory are free.  The host never waits for the step it has just
+// enqueued: step i+1 is built and enqueued while step i runs, and only then
+// does the thread wait for step i and hand out the results of the requests
+// it finished.  Per-request memory comes from the stream-ordered allocator
+// and is cleared, compacted and released on the second stream, so admission
+// and completion do not synchronise the device either.  Field tables stay
+// resident in the process-wide table cache.  Each request owns its histogram
+// hash; slices of one request add into it across steps.  Results do not
 // depend on how requests were mixed: every slice adds exact integer counts.
 #include "hwc_internal.cuh"
 
@@ -31,6 +35,7 @@ struct Request {
     uint64_t ticket = 0;
     hwc_job_t job{};
     KJob kj{};
+    KJob *d_one = nullptr;   // device copy of kj (clear, compact)
     uint64_t next_tile = 0;
     std::vector<void *> allocs;
     uint64_t bytes = 0;
@@ -38,8 +43,22 @@ struct Request {
     int rc = HWC_OK;
     std::string err;
     hwc_hist *result = nullptr;
+    // the compacted (key, count) list copied back; the sorted histogram is
+    // built from it in the thread that collects the result
+    std::vector<unsigned long long> rkeys, rcnt;
+    uint64_t rtotal = 0;
     bool collected = false;
     Clock::time_point t_submit, t_admit, t_done;
+};
+
+// a step on the device whose results are not yet handed out
+struct Inflight {
+    bool valid = false;
+    std::vector<Request *> reqs;
+    std::vector<uint64_t> took;
+    std::vector<Request *> finishing;   // requests whose last tiles the step runs
+    double evals = 0;
+    int rc = HWC_OK;
 };
 
 }  // namespace
@@ -47,12 +66,14 @@ struct Request {
 struct hwc_server {
     hwc_server_config_t cfg{};
     int device = 0;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;   // steps
+    cudaStream_t aux = nullptr;      // per-request allocation, clearing, compaction, release
     std::thread th;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<Request *> pending;
     std::vector<Request *> active;
+    uint32_t retiring = 0;           // requests whose last step is still in flight
     std::map<uint64_t, Request *> all;
     uint64_t next_ticket = 1;
     bool stop = false;
@@ -61,8 +82,11 @@ struct hwc_server {
     KJob *d_jobs = nullptr;
     uint64_t *d_item_start = nullptr;     // [2 * max_active]
     unsigned long long *d_counters = nullptr;   // [max_active]
-    KJob *h_jobs = nullptr;          // pinned staging
-    uint64_t *h_item_start = nullptr;
+    KJob *h_jobs[2] = {};            // pinned staging, one per step in flight
+    uint64_t *h_item_start[2] = {};
+    cudaEvent_t ev_t0[2] = {}, ev_t1[2] = {};
+    cudaEvent_t ev_admit = nullptr;
+    cudaMemPool_t pool = nullptr;    // per-request memory (kept mapped between requests)
     std::map<std::pair<int, uint32_t>, LaunchShape> shapes;
     unsigned long long *d_wkeys = nullptr;   // two-level kernel: member keys per resident warp
     uint64_t wkeys_slots = 0;
@@ -76,33 +100,38 @@ namespace {
 constexpr double kStepMs = 4.0;
 constexpr double kFirstEvalsPerMs = 1e9;
 
-// nominal point evaluations of one tile of a job: members per tile (q^2
-// for the two-level fan-out, q for the c_0 fan-out, 32 per member tile)
-// times sum_k q^k
+// point evaluations of one tile of a job: members per tile (q^2 for the
+// two-level fan-out, q for the c_0 fan-out, 32 per member tile) times the
+// points the kernels evaluate per member (one per Frobenius orbit)
 double tile_evals(const KJob &kj)
 {
     const double members = kj.method == 2 ? (double)kj.q * kj.q : (kj.method == 1 ? (double)kj.q : (double)kTileMembers);
     double pts = 0;
-    for (uint32_t k = 0; k < kj.g; ++k) pts += kj.Q[k];
+    for (uint32_t k = 0; k < kj.g; ++k) pts += kj.npts[k] + 1;
     return members * pts;
 }
 
-void free_request_device(Request *r)
+void free_request_device(hwc_server *s, Request *r)
 {
-    for (void *p : r->allocs) cudaFree(p);
+    for (void *p : r->allocs) cudaFreeAsync(p, s->aux);
     r->allocs.clear();
 }
 
-template <class T>
-int ralloc(Request *r, T **p, uint64_t n)
+// one stream-ordered allocation per request, carved into its arrays
+int ralloc_all(hwc_server *s, Request *r, const uint64_t *bytes, void **ptrs, int n)
 {
+    uint64_t total = 0, off[16];
+    for (int i = 0; i < n; ++i) {
+        off[i] = total;
+        total += (bytes[i] + 255) / 256 * 256;
+    }
     void *v = nullptr;
-    if (cudaMalloc(&v, std::max<uint64_t>(n, 1) * sizeof(T)) != cudaSuccess) {
+    if (cudaMallocFromPoolAsync(&v, total, s->pool, s->aux) != cudaSuccess) {
         cudaGetLastError();
-        return set_error(HWC_ERR_NOMEM, "cudaMalloc failed");
+        return set_error(HWC_ERR_NOMEM, "cudaMallocFromPoolAsync of %llu bytes failed", (unsigned long long)total);
     }
     r->allocs.push_back(v);
-    *p = (T *)v;
+    for (int i = 0; i < n; ++i) ptrs[i] = (char *)v + off[i];
     return HWC_OK;
 }
 
@@ -120,42 +149,50 @@ int shape_for(hwc_server *s, int D, uint32_t method, uint32_t words, uint32_t sm
     return HWC_OK;
 }
 
-// admission: allocate the request's hash and clear it (server thread)
+// admission (server thread): the request's hash, allocated and cleared on the
+// second stream; the step stream waits for it before its next launch
 int admit(hwc_server *s, Request *r)
 {
     KJob &kj = r->kj;
-    const uint32_t cap = kj.hmask + 1;
-    int rc;
-    if ((rc = ralloc(r, &kj.hkeys, cap)) || (rc = ralloc(r, &kj.hcounts, cap)) ||
-        (rc = ralloc(r, &kj.stats, 4)) || (rc = ralloc(r, &kj.out_keys, cap)) ||
-        (rc = ralloc(r, &kj.out_counts, cap)) || (rc = ralloc(r, &kj.n_out, 1)))
-        return rc;
-    KJob *d_one = nullptr;
-    if ((rc = ralloc(r, &d_one, 1))) return rc;
-    HWC_CUDA_TRY(cudaMemcpyAsync(d_one, &kj, sizeof kj, cudaMemcpyHostToDevice, s->stream));
-    rc = launch_clear(d_one, 1, nullptr, 0, s->stream);
+    const uint64_t cap = kj.hmask + 1ull;
+    const uint64_t bytes[7] = {8 * cap, 8 * cap, 8 * 4, 8 * cap, 8 * cap, 8, sizeof(KJob)};
+    void *ptrs[7];
+    int rc = ralloc_all(s, r, bytes, ptrs, 7);
     if (rc) return rc;
-    HWC_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    kj.hkeys = (unsigned long long *)ptrs[0];
+    kj.hcounts = (unsigned long long *)ptrs[1];
+    kj.stats = (unsigned long long *)ptrs[2];
+    kj.out_keys = (unsigned long long *)ptrs[3];
+    kj.out_counts = (unsigned long long *)ptrs[4];
+    kj.n_out = (unsigned long long *)ptrs[5];
+    r->d_one = (KJob *)ptrs[6];
+    HWC_CUDA_TRY(cudaMemcpyAsync(r->d_one, &kj, sizeof kj, cudaMemcpyHostToDevice, s->aux));
+    rc = launch_clear(r->d_one, 1, nullptr, 0, s->aux);
+    if (rc) return rc;
+    HWC_CUDA_TRY(cudaEventRecord(s->ev_admit, s->aux));
+    HWC_CUDA_TRY(cudaStreamWaitEvent(s->stream, s->ev_admit, 0));
     return HWC_OK;
 }
 
-// finished request: compact its hash and build the host histogram
+// finished request (its last step is complete): compact its hash on the second
+// stream and copy the (key, count) list back
 int finish(hwc_server *s, Request *r)
 {
-    KJob *d_one = (KJob *)r->allocs.back();
-    int rc = launch_compact(d_one, 1, s->stream);
+    int rc = launch_compact(r->d_one, 1, s->aux);
     if (rc) return rc;
     unsigned long long st[3] = {}, n_out = 0;
-    HWC_CUDA_TRY(cudaMemcpyAsync(st, r->kj.stats, sizeof st, cudaMemcpyDeviceToHost, s->stream));
-    HWC_CUDA_TRY(cudaMemcpyAsync(&n_out, r->kj.n_out, sizeof n_out, cudaMemcpyDeviceToHost, s->stream));
-    HWC_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    HWC_CUDA_TRY(cudaMemcpyAsync(st, r->kj.stats, sizeof st, cudaMemcpyDeviceToHost, s->aux));
+    HWC_CUDA_TRY(cudaMemcpyAsync(&n_out, r->kj.n_out, sizeof n_out, cudaMemcpyDeviceToHost, s->aux));
+    HWC_CUDA_TRY(cudaStreamSynchronize(s->aux));
     if (st[2]) return set_error(HWC_ERR_TOO_LARGE, "histogram hash overflowed");
-    std::vector<unsigned long long> keys(n_out), cnt(n_out);
+    r->rkeys.resize(n_out);
+    r->rcnt.resize(n_out);
     if (n_out) {
-        HWC_CUDA_TRY(cudaMemcpy(keys.data(), r->kj.out_keys, n_out * 8, cudaMemcpyDeviceToHost));
-        HWC_CUDA_TRY(cudaMemcpy(cnt.data(), r->kj.out_counts, n_out * 8, cudaMemcpyDeviceToHost));
+        HWC_CUDA_TRY(cudaMemcpyAsync(r->rkeys.data(), r->kj.out_keys, n_out * 8, cudaMemcpyDeviceToHost, s->aux));
+        HWC_CUDA_TRY(cudaMemcpyAsync(r->rcnt.data(), r->kj.out_counts, n_out * 8, cudaMemcpyDeviceToHost, s->aux));
+        HWC_CUDA_TRY(cudaStreamSynchronize(s->aux));
     }
-    r->result = hist_from_keys(r->kj, keys.data(), cnt.data(), n_out, st[0]);
+    r->rtotal = st[0];
     return HWC_OK;
 }
 
@@ -166,22 +203,158 @@ void complete(hwc_server *s, Request *r, int rc)
     if (rc) r->err = hwc_last_error();
     r->state = 2;
     r->t_done = Clock::now();
-    free_request_device(r);
+    free_request_device(s, r);
     s->used_bytes -= std::min(s->used_bytes, r->bytes);
     s->cv_done.notify_all();
+}
+
+// Build one step over `step` (a slice of every request) into staging buffer
+// `buf` and enqueue it on the step stream; requests of one kernel group share
+// a persistent launch.  Advances each request's next tile.
+int enqueue_step(hwc_server *s, std::vector<Request *> &step, int buf, Inflight &inf)
+{
+    auto skey = [](const Request *x) { return std::make_tuple(x->kj.d, x->kj.method, x->kj.words); };
+    std::stable_sort(step.begin(), step.end(), [&](const Request *x, const Request *y) { return skey(x) < skey(y); });
+    const uint32_t n = (uint32_t)step.size();
+    inf.reqs = step;
+    inf.took.assign(n, 0);
+    // equal point evaluations per request, the step about kStepMs in all
+    const double req_evals = (s->evals_per_ms > 0 ? s->evals_per_ms : kFirstEvalsPerMs) * kStepMs / n;
+    int rc = HWC_OK;
+    uint32_t item_off = 0, ngroups = 0;
+    struct StepGroup {
+        int D;
+        uint32_t method, words;
+        uint32_t first, n, off;
+        uint64_t items;
+        uint32_t smem;
+        LaunchShape sh;
+    };
+    std::vector<StepGroup> groups;
+    KJob *hj = s->h_jobs[buf];
+    uint64_t *hs = s->h_item_start[buf];
+    for (uint32_t i = 0; i < n && rc == HWC_OK;) {
+        uint32_t e = i;
+        uint32_t smem = 0;
+        while (e < n && skey(step[e]) == skey(step[i])) smem = std::max(smem, step[e++]->kj.smem_bytes);
+        StepGroup G{(int)step[i]->kj.d, step[i]->kj.method, step[i]->kj.words, i, e - i, item_off, 0, smem,
+                    LaunchShape()};
+        if (G.method == 2) {
+            std::vector<Fan2Need> needs;
+            for (uint32_t r = i; r < e; ++r) needs.push_back({step[r]->kj.warp_off, step[r]->kj.warp_bytes});
+            rc = choose_shape_fan2(G.D, needs.data(), needs.size(), &G.sh, &G.smem);
+            if (rc == HWC_OK && (uint64_t)G.sh.grid * (G.sh.block / 32) * 961ull > s->wkeys_slots)
+                rc = set_error(HWC_ERR_TOO_LARGE, "server key scratch too small");
+        } else {
+            rc = shape_for(s, G.D, G.method, G.words, smem, &G.sh);
+        }
+        if (rc) break;
+        // per request: its share of the step's point evaluations (req_evals),
+        // and at least its share of about 8 work items per CTA of the launch
+        // (the tail of a launch then weighs little); with step_items set by
+        // the caller, exactly its share of step_items items per launch
+        uint64_t budget = s->cfg.step_items ? s->cfg.step_items : (uint64_t)G.sh.grid * 8;
+        budget *= (uint64_t)G.sh.item_tiles;
+        const uint64_t share = std::max<uint64_t>(G.sh.item_tiles, budget / (e - i));
+        uint64_t items = 0;
+        for (uint32_t r = i; r < e; ++r) {
+            Request *q = step[r];
+            KJob sl = q->kj;
+            const uint64_t left = q->kj.n_tiles - q->next_tile;
+            uint64_t want = share;
+            if (!s->cfg.step_items) want = std::max<uint64_t>(want, (uint64_t)(req_evals / tile_evals(q->kj)) + 1);
+            const uint64_t t = std::min(left, want);
+            inf.took[r] = t;
+            inf.evals += (double)t * tile_evals(q->kj);
+            if (q->kj.method != 0) {
+                // fan-out tiles are groups; the member range stays the request's
+                sl.first_group = q->kj.first_group + q->next_tile;
+            } else {
+                sl.first = q->kj.first + q->next_tile * kTileMembers;
+                sl.count = std::min<uint64_t>(q->kj.count - q->next_tile * kTileMembers, t * kTileMembers);
+            }
+            sl.n_tiles = t;
+            sl.wkeys = s->d_wkeys;
+            sl.wkeys_stride = 961;   // q <= 31
+            hj[r] = sl;
+            hs[item_off + (r - i)] = items;
+            items += (t + G.sh.item_tiles - 1) / G.sh.item_tiles;
+        }
+        hs[item_off + (e - i)] = items;
+        G.items = items;
+        item_off += (e - i) + 1;
+        groups.push_back(G);
+        ++ngroups;
+        i = e;
+    }
+    if (rc) return rc;
+    // descriptors from pinned memory, then the launches, all on the step stream
+    HWC_CUDA_TRY(cudaMemcpyAsync(s->d_jobs, hj, n * sizeof(KJob), cudaMemcpyHostToDevice, s->stream));
+    HWC_CUDA_TRY(cudaMemcpyAsync(s->d_item_start, hs, item_off * sizeof(uint64_t), cudaMemcpyHostToDevice, s->stream));
+    HWC_CUDA_TRY(cudaMemsetAsync(s->d_counters, 0, ngroups * sizeof(unsigned long long), s->stream));
+    HWC_CUDA_TRY(cudaEventRecord(s->ev_t0[buf], s->stream));
+    for (size_t g = 0; g < groups.size(); ++g) {
+        const StepGroup &G = groups[g];
+        rc = launch_persistent(G.D, G.method, G.words, s->d_jobs + G.first, s->d_item_start + G.off, G.n, G.items,
+                               s->d_counters + g, G.smem, G.sh, s->stream);
+        if (rc) return rc;
+    }
+    HWC_CUDA_TRY(cudaEventRecord(s->ev_t1[buf], s->stream));
+    for (uint32_t i = 0; i < n; ++i) {
+        Request *r = step[i];
+        r->next_tile += inf.took[i];
+        if (r->next_tile >= r->kj.n_tiles) inf.finishing.push_back(r);
+    }
+    return HWC_OK;
+}
+
+// wait for a step in flight and hand out the requests it finished
+void retire_step(hwc_server *s, Inflight &inf, int buf)
+{
+    int rc = inf.rc;
+    if (rc == HWC_OK) {
+        cudaError_t ce = cudaEventSynchronize(s->ev_t1[buf]);
+        if (ce != cudaSuccess) rc = set_error(HWC_ERR_CUDA, "step: %s", cudaGetErrorString(ce));
+    }
+    if (rc == HWC_OK) {   // the step's device rate updates the running mean
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, s->ev_t0[buf], s->ev_t1[buf]) == cudaSuccess && ms > 0 && inf.evals > 0)
+            s->evals_per_ms = s->evals_per_ms > 0 ? 0.5 * s->evals_per_ms + 0.5 * (inf.evals / ms) : inf.evals / ms;
+    }
+    if (rc) {   // nothing may still run on a request's memory when it is released
+        cudaStreamSynchronize(s->stream);
+        cudaGetLastError();
+    }
+    std::vector<int> frc(inf.finishing.size(), rc);
+    if (rc == HWC_OK)
+        for (size_t i = 0; i < inf.finishing.size(); ++i) frc[i] = finish(s, inf.finishing[i]);
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (rc) {   // a failed step fails every request it touched
+        for (Request *r : inf.reqs) {
+            if (r->state == 2) continue;
+            s->active.erase(std::remove(s->active.begin(), s->active.end(), r), s->active.end());
+            complete(s, r, rc);
+        }
+    }
+    for (size_t i = 0; i < inf.finishing.size(); ++i)
+        if (inf.finishing[i]->state != 2) complete(s, inf.finishing[i], frc[i]);
+    s->retiring -= std::min<uint32_t>(s->retiring, (uint32_t)inf.finishing.size());
+    inf = Inflight();
 }
 
 void server_loop(hwc_server *s)
 {
     cudaSetDevice(s->device);
     const uint32_t max_active = std::max<uint32_t>(1, s->cfg.max_active);
+    Inflight prev;
+    int buf = 0;
     for (;;) {
         std::vector<Request *> step;
         {
             std::unique_lock<std::mutex> lk(s->mu);
             for (;;) {
                 // admit while a slot and memory are free
-                while (!s->pending.empty() && s->active.size() < max_active) {
+                while (!s->pending.empty() && s->active.size() + s->retiring < max_active) {
                     Request *r = s->pending.front();
                     if (r->bytes > s->cfg.device_bytes) {
                         s->pending.pop_front();
@@ -205,134 +378,34 @@ void server_loop(hwc_server *s)
                     r->t_admit = Clock::now();
                     s->active.push_back(r);
                 }
-                if (!s->active.empty()) break;
+                if (!s->active.empty() || prev.valid) break;
                 if (s->stop && s->pending.empty()) return;
                 s->cv_work.wait(lk);
             }
             step = s->active;
         }
-
-        // one device step: a fair share of tiles of every active request; requests
-        // of one degree share a persistent launch
-        auto skey = [](const Request *x) { return std::make_tuple(x->kj.d, x->kj.method, x->kj.words); };
-        std::stable_sort(step.begin(), step.end(),
-                         [&](const Request *x, const Request *y) { return skey(x) < skey(y); });
-        const uint32_t n = (uint32_t)step.size();
-        std::vector<uint64_t> took(n, 0);
-        // equal point evaluations per request, the step about kStepMs in all
-        const double req_evals = (s->evals_per_ms > 0 ? s->evals_per_ms : kFirstEvalsPerMs) * kStepMs / n;
-        int rc = HWC_OK;
-        uint32_t item_off = 0, ngroups = 0;
-        struct StepGroup {
-            int D;
-            uint32_t method, words;
-            uint32_t first, n, off;
-            uint64_t items;
-            uint32_t smem;
-            LaunchShape sh;
-        };
-        std::vector<StepGroup> groups;
-        for (uint32_t i = 0; i < n && rc == HWC_OK;) {
-            uint32_t e = i;
-            uint32_t smem = 0;
-            while (e < n && skey(step[e]) == skey(step[i])) smem = std::max(smem, step[e++]->kj.smem_bytes);
-            StepGroup G{(int)step[i]->kj.d, step[i]->kj.method, step[i]->kj.words, i, e - i, item_off, 0, smem,
-                        LaunchShape()};
-            if (G.method == 2) {
-                std::vector<Fan2Need> needs;
-                for (uint32_t r = i; r < e; ++r) needs.push_back({step[r]->kj.warp_off, step[r]->kj.warp_bytes});
-                rc = choose_shape_fan2(G.D, needs.data(), needs.size(), &G.sh, &G.smem);
-                if (rc == HWC_OK &&
-                    (uint64_t)G.sh.grid * (G.sh.block / 32) * 961ull > s->wkeys_slots)
-                    rc = set_error(HWC_ERR_TOO_LARGE, "server key scratch too small");
+        // enqueue the next step while the previous one runs
+        Inflight cur;
+        if (!step.empty()) {
+            cur.valid = true;
+            cur.rc = enqueue_step(s, step, buf, cur);
+            std::lock_guard<std::mutex> lk(s->mu);
+            if (cur.rc) {
+                cur.finishing.clear();
             } else {
-                rc = shape_for(s, G.D, G.method, G.words, smem, &G.sh);
+                for (Request *r : cur.finishing)
+                    s->active.erase(std::remove(s->active.begin(), s->active.end(), r), s->active.end());
+                s->retiring += (uint32_t)cur.finishing.size();
             }
-            if (rc) break;
-            // per request: its share of the step's point evaluations (req_evals),
-            // and at least its share of about 8 work items per CTA of the launch
-            // (the tail of a launch then weighs little); with step_items set by
-            // the caller, exactly its share of step_items items per launch
-            uint64_t budget = s->cfg.step_items ? s->cfg.step_items : (uint64_t)G.sh.grid * 8;
-            budget *= (uint64_t)G.sh.item_tiles;
-            const uint64_t share = std::max<uint64_t>(G.sh.item_tiles, budget / (e - i));
-            uint64_t items = 0;
-            for (uint32_t r = i; r < e; ++r) {
-                Request *q = step[r];
-                KJob sl = q->kj;
-                const uint64_t left = q->kj.n_tiles - q->next_tile;
-                uint64_t want = share;
-                if (!s->cfg.step_items)
-                    want = std::max<uint64_t>(want, (uint64_t)(req_evals / tile_evals(q->kj)) + 1);
-                const uint64_t t = std::min(left, want);
-                took[r] = t;
-                if (q->kj.method != 0) {
-                    // fan-out tiles are groups; the member range stays the request's
-                    sl.first_group = q->kj.first_group + q->next_tile;
-                } else {
-                    sl.first = q->kj.first + q->next_tile * kTileMembers;
-                    sl.count = std::min<uint64_t>(q->kj.count - q->next_tile * kTileMembers, t * kTileMembers);
-                }
-                sl.n_tiles = t;
-                sl.wkeys = s->d_wkeys;
-                sl.wkeys_stride = 961;   // q <= 31
-                s->h_jobs[r] = sl;
-                s->h_item_start[item_off + (r - i)] = items;
-                items += (t + G.sh.item_tiles - 1) / G.sh.item_tiles;
-            }
-            s->h_item_start[item_off + (e - i)] = items;
-            G.items = items;
-            item_off += (e - i) + 1;
-            groups.push_back(G);
-            ++ngroups;
-            i = e;
+            ++s->steps;
         }
-        cudaError_t ce = cudaSuccess;
-        const Clock::time_point t_step = Clock::now();
-        if (rc == HWC_OK) {
-            ce = cudaMemcpyAsync(s->d_jobs, s->h_jobs, n * sizeof(KJob), cudaMemcpyHostToDevice, s->stream);
-            if (ce == cudaSuccess)
-                ce = cudaMemcpyAsync(s->d_item_start, s->h_item_start, item_off * sizeof(uint64_t),
-                                     cudaMemcpyHostToDevice, s->stream);
-            if (ce == cudaSuccess)
-                ce = cudaMemsetAsync(s->d_counters, 0, ngroups * sizeof(unsigned long long), s->stream);
-            if (ce != cudaSuccess) rc = set_error(HWC_ERR_CUDA, "step setup: %s", cudaGetErrorString(ce));
+        if (prev.valid) retire_step(s, prev, buf ^ 1);
+        if (cur.valid && cur.rc) {   // nothing of it runs: fail its requests now
+            retire_step(s, cur, buf);
+            continue;
         }
-        for (size_t g = 0; rc == HWC_OK && g < groups.size(); ++g) {
-            const StepGroup &G = groups[g];
-            rc = launch_persistent(G.D, G.method, G.words, s->d_jobs + G.first, s->d_item_start + G.off, G.n,
-                                   G.items, s->d_counters + g, G.smem, G.sh, s->stream);
-        }
-        if (rc == HWC_OK) {
-            ce = cudaStreamSynchronize(s->stream);
-            if (ce != cudaSuccess) rc = set_error(HWC_ERR_CUDA, "step: %s", cudaGetErrorString(ce));
-        }
-        if (rc == HWC_OK) {   // the step's rate updates the running mean
-            const double ms = std::chrono::duration<double, std::milli>(Clock::now() - t_step).count();
-            double ev = 0;
-            for (uint32_t i = 0; i < n; ++i) ev += (double)took[i] * tile_evals(step[i]->kj);
-            if (ms > 0 && ev > 0)
-                s->evals_per_ms = s->evals_per_ms > 0 ? 0.5 * s->evals_per_ms + 0.5 * (ev / ms) : ev / ms;
-        }
-        ++s->steps;
-
-        std::lock_guard<std::mutex> lk(s->mu);
-        std::vector<Request *> still;
-        for (uint32_t i = 0; i < n; ++i) {
-            Request *r = step[i];
-            if (rc) {
-                complete(s, r, rc);
-                continue;
-            }
-            r->next_tile += took[i];
-            if (r->next_tile >= r->kj.n_tiles) {
-                int frc = finish(s, r);
-                complete(s, r, frc);
-            } else {
-                still.push_back(r);
-            }
-        }
-        s->active.swap(still);
+        prev = cur;
+        buf ^= 1;
     }
 }
 
@@ -350,12 +423,23 @@ extern "C" int hwc_serve_open(const hwc_server_config_t *cfg, hwc_server_t **out
     if (!s->cfg.max_active) s->cfg.max_active = 64;
     cudaGetDevice(&s->device);
     const uint32_t m = s->cfg.max_active;
-    bool ok = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) == cudaSuccess &&
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = s->device;
+    const uint64_t keep = ~0ull;   // keep freed request memory mapped for the next requests
+    bool ok = cudaMemPoolCreate(&s->pool, &props) == cudaSuccess &&
+              cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, (void *)&keep) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&s->ev_admit, cudaEventDisableTiming) == cudaSuccess &&
               cudaMalloc(&s->d_jobs, m * sizeof(KJob)) == cudaSuccess &&
               cudaMalloc(&s->d_item_start, 2 * (m + 1) * sizeof(uint64_t)) == cudaSuccess &&
-              cudaMalloc(&s->d_counters, m * sizeof(unsigned long long)) == cudaSuccess &&
-              cudaMallocHost(&s->h_jobs, m * sizeof(KJob)) == cudaSuccess &&
-              cudaMallocHost(&s->h_item_start, 2 * (m + 1) * sizeof(uint64_t)) == cudaSuccess;
+              cudaMalloc(&s->d_counters, m * sizeof(unsigned long long)) == cudaSuccess;
+    for (int b = 0; b < 2 && ok; ++b)
+        ok = cudaMallocHost(&s->h_jobs[b], m * sizeof(KJob)) == cudaSuccess &&
+             cudaMallocHost(&s->h_item_start[b], 2 * (m + 1) * sizeof(uint64_t)) == cudaSuccess &&
+             cudaEventCreate(&s->ev_t0[b]) == cudaSuccess && cudaEventCreate(&s->ev_t1[b]) == cudaSuccess;
     // every resident warp of the GPU (at most 64 per SM) may hold q^2 <= 961 keys
     s->wkeys_slots = (uint64_t)device_sm_count() * 64 * 961;
     ok = ok && cudaMalloc(&s->d_wkeys, s->wkeys_slots * sizeof(unsigned long long)) == cudaSuccess;
@@ -415,8 +499,14 @@ extern "C" int hwc_serve_poll(hwc_server_t *s, uint64_t ticket, uint32_t timeout
     if (r->rc) return set_error(r->rc, "%s", r->err.c_str());
     if (r->collected) return set_error(HWC_ERR_STATE, "result of %llu already collected", (unsigned long long)ticket);
     r->collected = true;
-    *out = r->result;
-    r->result = nullptr;
+    // the sorted histogram, built here in the caller's thread (not the server's)
+    std::vector<unsigned long long> keys, cnt;
+    keys.swap(r->rkeys);
+    cnt.swap(r->rcnt);
+    const KJob kj = r->kj;
+    const uint64_t total = r->rtotal;
+    lk.unlock();
+    *out = hist_from_keys(kj, keys.data(), cnt.data(), keys.size(), total);
     return HWC_OK;
 }
 
@@ -444,17 +534,26 @@ extern "C" int hwc_serve_close(hwc_server_t *s)
     s->cv_work.notify_all();
     if (s->th.joinable()) s->th.join();
     for (auto &kv : s->all) {
-        free_request_device(kv.second);
+        if (s->aux) free_request_device(s, kv.second);
         hwc_hist_free(kv.second->result);
         delete kv.second;
     }
+    if (s->aux) cudaStreamSynchronize(s->aux);
+    if (s->stream) cudaStreamSynchronize(s->stream);
     cudaFree(s->d_jobs);
     cudaFree(s->d_item_start);
     cudaFree(s->d_counters);
     cudaFree(s->d_wkeys);
-    if (s->h_jobs) cudaFreeHost(s->h_jobs);
-    if (s->h_item_start) cudaFreeHost(s->h_item_start);
+    for (int b = 0; b < 2; ++b) {
+        if (s->h_jobs[b]) cudaFreeHost(s->h_jobs[b]);
+        if (s->h_item_start[b]) cudaFreeHost(s->h_item_start[b]);
+        if (s->ev_t0[b]) cudaEventDestroy(s->ev_t0[b]);
+        if (s->ev_t1[b]) cudaEventDestroy(s->ev_t1[b]);
+    }
+    if (s->ev_admit) cudaEventDestroy(s->ev_admit);
     if (s->stream) cudaStreamDestroy(s->stream);
+    if (s->aux) cudaStreamDestroy(s->aux);
+    if (s->pool) cudaMemPoolDestroy(s->pool);
     delete s;
     return HWC_OK;
 }

@@ -279,6 +279,26 @@ __global__ void k_zech(uint32_t p, uint32_t L, const uint32_t *__restrict__ anti
     }
 }
 
+// 17-bit layout of the Zech table for fields whose logs need 17 bits: one
+// thread per 32 entries writes their low 16 bits and the word of their high
+// bits.  Entry L/2 (1 + alpha^(L/2) = 0, Z = L) and entry L carry the marker
+// 0x1FFFF, which no log reaches (L < 0x1FFFF).
+__global__ void k_zech17(uint32_t L, const uint32_t *__restrict__ zech, uint16_t *lo, uint32_t *hi)
+{
+    const uint32_t nhi = (L + 32) / 32;
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nhi; w += gridDim.x * blockDim.x) {
+        uint32_t bits = 0;
+        for (uint32_t i = 0; i < 32; ++i) {
+            const uint32_t n = 32 * w + i;
+            if (n > L) break;
+            const uint32_t v = (n == L || zech[n] == L) ? 0x1FFFFu : zech[n];
+            lo[n] = (uint16_t)(v & 0xFFFFu);
+            bits |= (v >> 16) << i;
+        }
+        hi[w] = bits;
+    }
+}
+
 // fan-out rows: bit c of row l = [chi(alpha^l + e_c) = -1], e_c the digit c in F_Q;
 // alpha^l + e_c = e_c (1 + alpha^(l - log e_c)).  Top bit: alpha^l + e_c = 0 for
 // some c (then alpha^l lies in F_q^x).
@@ -439,6 +459,34 @@ __global__ void k_coef_log(ElemArgs a, uint64_t th, const uint32_t *__restrict__
 
 // ---------------------------------------------------------------------
 
+// Logs j in [0, L) of one element per Frobenius orbit of the elements of F_Q^x
+// of exact degree k over F_q (Q = q^k, L = Q - 1): with x = alpha^j the orbit
+// of x is {alpha^(j q^i mod L)}, and x has degree m | k over F_q exactly when
+// j (q^m - 1) = 0 mod L.  The smallest j of each orbit of size k, ascending.
+// Their number is the number of monic irreducible polynomials of degree k over
+// F_q.
+std::vector<uint32_t> orbit_reps(uint32_t q, uint32_t k, uint32_t L)
+{
+    std::vector<uint32_t> out;
+    uint64_t qm[kMaxG + 1];
+    qm[0] = 1;
+    for (uint32_t m = 1; m <= k; ++m) qm[m] = qm[m - 1] * q;
+    for (uint32_t j = 0; j < L; ++j) {
+        bool sub = false;
+        for (uint32_t m = 1; m < k && !sub; ++m)
+            if (k % m == 0 && (uint64_t)j * (qm[m] - 1) % L == 0) sub = true;
+        if (sub) continue;
+        bool least = true;
+        uint64_t y = j;
+        for (uint32_t i = 1; i < k && least; ++i) {
+            y = y * q % L;
+            if (y < j) least = false;
+        }
+        if (least) out.push_back(j);
+    }
+    return out;
+}
+
 void tables_destroy(Tables *t)
 {
     if (!t) return;
@@ -452,6 +500,9 @@ void tables_destroy(Tables *t)
     cudaFree(t->d_zech2);
     cudaFree(t->d_zech2w);
     cudaFree(t->d_zech3);
+    cudaFree(t->d_z17lo);
+    cudaFree(t->d_z17hi);
+    cudaFree(t->d_reps);
     cudaFree(t->d_rows32);
     cudaFree(t->d_rows64);
     cudaFree(t->d_zdig);
@@ -529,6 +580,10 @@ int tables_build(uint32_t q, uint32_t k, Tables **out)
         ok = cudaMalloc(&t->d_zech2, sizeof(uint16_t) * (2ull * L + 1)) == cudaSuccess;
     if (ok && 3ull * L < 65536ull)
         ok = cudaMalloc(&t->d_zech3, sizeof(uint16_t) * (3ull * L + 1)) == cudaSuccess;
+    const bool z17 = 2ull * L >= 65536ull && L < 0x1FFFFu;
+    if (ok && z17)
+        ok = cudaMalloc(&t->d_z17lo, sizeof(uint16_t) * (L + 1ull)) == cudaSuccess &&
+             cudaMalloc(&t->d_z17hi, sizeof(uint32_t) * ((L + 32ull) / 32)) == cudaSuccess;
     if (!ok) {
         cudaFree(d_best);
         return fail(set_error(HWC_ERR_NOMEM, "cudaMalloc of tables for Q=%u failed", t->Q));
@@ -543,6 +598,8 @@ int tables_build(uint32_t q, uint32_t k, Tables **out)
     k_antilog<<<(unsigned)((nthr + 127) / 128), 128>>>(mp, L, B, t->d_antilog, t->d_log);
     k_zech<<<std::max(1u, std::min(4096u, (unsigned)((3ull * L + 256) / 256))), 256>>>(
         p, L, t->d_antilog, t->d_log, t->d_zech, t->d_zech2, t->d_zech2w, t->d_zech3);
+    if (z17) k_zech17<<<std::max(1u, std::min(1024u, (L + 32 * 128) / (32 * 128))), 128>>>(L, t->d_zech, t->d_z17lo,
+                                                                                           t->d_z17hi);
 
     // 3. logs of the F_q digits
     ElemArgs ea{};
@@ -592,6 +649,16 @@ int tables_build(uint32_t q, uint32_t k, Tables **out)
             cudaMemset(t->d_coord2, 0, sizeof(uint32_t) * L);   // every entry is written; zero keeps digits in range
             k_coord2<<<1, 256>>>(q, L, t->d_zech, t->d_coef_log, t->d_coord2);
         }
+    }
+    // 5. one point per Frobenius orbit of the elements of exact degree k
+    if (k >= 2) {
+        std::vector<uint32_t> reps = orbit_reps(q, k, L);
+        t->n_reps = (uint32_t)reps.size();
+        if (cudaMalloc(&t->d_reps, sizeof(uint32_t) * reps.size()) != cudaSuccess) {
+            cudaFree(d_best);
+            return fail(set_error(HWC_ERR_NOMEM, "cudaMalloc of the orbit list of F_%u failed", t->Q));
+        }
+        cudaMemcpy(t->d_reps, reps.data(), sizeof(uint32_t) * reps.size(), cudaMemcpyHostToDevice);
     }
     cudaError_t ce = cudaDeviceSynchronize();
     cudaFree(d_best);

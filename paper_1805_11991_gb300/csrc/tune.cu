@@ -24,7 +24,7 @@ std::mutex g_mu;
 std::map<Key, TuneChoice> g_cache;
 bool g_file_read = false;
 
-constexpr uint32_t kFlagMask = HWC_FLAG_HORNER | HWC_FLAG_FAN1;
+constexpr uint32_t kFlagMask = HWC_FLAG_HORNER | HWC_FLAG_FAN1 | HWC_FLAG_ALL_POINTS | HWC_FLAG_LAMBDA;
 
 Key key_of(const hwc_job_t &jb, uint32_t flags)
 {
@@ -78,7 +78,7 @@ std::vector<TuneChoice> candidates(const hwc_job_t &jb, uint32_t flags)
 {
     std::vector<TuneChoice> v;
     const bool sampled = jb.family.kind == HWC_FAM_MONIC_NOSUB_SAMPLED;
-    if (sampled || (flags & HWC_FLAG_HORNER) || jb.q > 63) return {make(0, 0, false)};
+    if (sampled || (flags & (HWC_FLAG_HORNER | HWC_FLAG_LAMBDA)) || jb.q > 63) return {make(0, 0, false)};
     if (jb.q <= 31 && !(flags & HWC_FLAG_FAN1)) {
         v.push_back(make(2, 0, false));   // the default: most resident warps
         for (int w : {16, 8}) v.push_back(make(2, w, false));
@@ -105,10 +105,12 @@ bool verbose()
 }
 
 // kernel time (ms) of one candidate on the probe, or a negative value
-double time_candidate(const hwc_job_t &probe, const TuneChoice &c, uint32_t *method)
+double time_candidate(const hwc_job_t &probe, const TuneChoice &c, uint32_t *method, uint32_t flags)
 {
     hwc_batch *b = nullptr;
-    if (batch_create_with(&probe, 1, HWC_FLAG_PLAIN | HWC_FLAG_TIMING, &c, &b) != HWC_OK) return -1;
+    if (batch_create_with(&probe, 1, HWC_FLAG_PLAIN | HWC_FLAG_TIMING | (flags & HWC_FLAG_ALL_POINTS), &c, &b) !=
+        HWC_OK)
+        return -1;
     double best = -1;
     hwc_batch_job_method(b, 0, method);
     for (int rep = 0; rep < 3; ++rep) {   // the first is a warm-up
@@ -153,7 +155,7 @@ int tune_choice(const hwc_job_t &jb, uint32_t flags, TuneChoice *out)
     std::vector<uint32_t> seen;   // (method, warps, no_triple) already timed
     for (const TuneChoice &c : cand) {
         uint32_t method = 0;
-        const double ms = time_candidate(probe, c, &method);
+        const double ms = time_candidate(probe, c, &method, flags);
         if (ms < 0) {   // this candidate could not run (e.g. out of memory): skip it
             cudaGetLastError();
             continue;

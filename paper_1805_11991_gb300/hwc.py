@@ -21,6 +21,8 @@ MAX_Q = 262144
 
 FAM_ALL_DEG, FAM_MONIC_NOSUB, FAM_MONIC_NOSUB_SAMPLED = 0, 1, 2
 FLAG_PLAIN, FLAG_GRAPH, FLAG_HORNER, FLAG_NO_TUNE, FLAG_TIMING, FLAG_FAN1 = 0x1, 0x2, 0x4, 0x8, 0x10, 0x20
+FLAG_ALL_POINTS = 0x40
+FLAG_LAMBDA = 0x80
 
 
 class HwcError(RuntimeError):
@@ -80,6 +82,7 @@ def load(build_if_missing: bool = True):
             "hwc_hist_size": (c_int, [vp, P(u64), P(u64), P(u64)]),
             "hwc_hist_genus": (c_int, [vp, P(u32)]),
             "hwc_hist_read": (c_int, [vp, P(ctypes.c_int32), P(u64)]),
+            "hwc_hist_lambda": (c_int, [vp, P(u64)]),
             "hwc_hist_merge": (c_int, [vp, vp]),
             "hwc_hist_from_arrays": (c_int, [u32, u64, P(ctypes.c_int32), P(u64), u64, P(vp)]),
             "hwc_hist_free": (None, [vp]),
@@ -181,6 +184,7 @@ class Histogram:
     mult: np.ndarray        # uint64 [n]
     n_squarefree: int
     n_total: int
+    lam: np.ndarray | None = None   # uint64 [n]: factorisation pattern codes (HWC_FLAG_LAMBDA)
 
     def as_dict(self):
         return {tuple(int(v) for v in row): int(m) for row, m in zip(self.counts, self.mult)}
@@ -196,7 +200,10 @@ def _take_hist(h: ctypes.c_void_p) -> Histogram:
         mult = np.zeros(n.value, np.uint64)
         _check(_lib.hwc_hist_read(h, counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                   mult.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
-        return Histogram(g.value, counts, mult, nsq.value, ntot.value)
+        lam = np.zeros(n.value, np.uint64)
+        if _lib.hwc_hist_lambda(h, lam.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))) != OK:
+            lam = None
+        return Histogram(g.value, counts, mult, nsq.value, ntot.value, lam)
     finally:
         _lib.hwc_hist_free(h)
 

@@ -25,7 +25,9 @@ CALLS = [
 ]
 
 
-def _noalloc(spec, tables_cache, max_entries=20000):
+def _noalloc(spec, tables_cache, max_entries=20000, free_bytes=None):
+    """Run one call; with free_bytes (a list) append the device's free memory
+    just before and just after the call (torch's allocator idle meanwhile)."""
     import torch
     tabs = []
     for k in range(1, spec.g + 1):
@@ -37,8 +39,13 @@ def _noalloc(spec, tables_cache, max_entries=20000):
     mult = torch.zeros(max_entries, dtype=torch.int64, device="cuda")
     n_out = torch.zeros(3, dtype=torch.int64, device="cuda")
     fam = hwc.make_family(spec.kind, spec.degree, spec.seed, spec.sample_count)
+    torch.cuda.synchronize()
+    if free_bytes is not None:
+        free_bytes.append(torch.cuda.mem_get_info()[0])
     hwc.count_noalloc(spec.g, spec.q, fam, spec.first, spec.n(), tabs, max_entries,
                       counts.data_ptr(), mult.data_ptr(), n_out.data_ptr())
+    if free_bytes is not None:
+        free_bytes.append(torch.cuda.mem_get_info()[0])
     n, nsq, ntot = (int(v) for v in n_out.cpu())
     c = counts[:n].cpu().numpy()
     m = mult[:n].cpu().numpy().astype(np.uint64)
@@ -50,13 +57,18 @@ def test_noalloc_matches_count_on_calls_in_a_row():
     import torch
     torch.cuda.init()
     cache = {}
-    for spec in CALLS:
+    for i, spec in enumerate(CALLS):
         fam = hwc.make_family(spec.kind, spec.degree, spec.seed, spec.sample_count)
         ref = hwc.count(spec.g, spec.q, fam, spec.first, spec.n())
-        c, m, nsq, ntot = _noalloc(spec, cache)
+        free = []
+        c, m, nsq, ntot = _noalloc(spec, cache, free_bytes=free)
         np.testing.assert_array_equal(c, ref.counts)
         np.testing.assert_array_equal(m, ref.mult)
         assert nsq == ref.n_squarefree and ntot == ref.n_total == spec.n()
+        # after the first call (which loads the kernels and looks up the
+        # scratch array on this device) a call takes no device memory
+        if i > 0:
+            assert free[0] == free[1], f"device free memory changed across the call: {free}"
 
 
 def test_noalloc_rejects_jobs_beyond_its_scratch():
