@@ -83,6 +83,12 @@ def _load():
                                         i32, i32, i32, i32, P32, P8]
         u32 = ctypes.c_uint32
         P64 = ctypes.POINTER(ctypes.c_uint64)
+        lib.orc_count_list.restype = i32
+        lib.orc_count_list.argtypes = [i32, i32, i32, u64, P32, i32, P32, P8, ctypes.POINTER(ctypes.c_uint64)]
+        lib.orc_lambda_codes.restype = i32
+        lib.orc_lambda_codes.argtypes = [i32, i32, i32, i32, u64, u64, u64, u64, i32, ctypes.POINTER(ctypes.c_uint64)]
+        lib.orc_factor_degrees.restype = i32
+        lib.orc_factor_degrees.argtypes = [vp, i32, P32, P32]
         lib.hwc_cpu_count.restype = i32
         lib.hwc_cpu_count.argtypes = [u32, u32, u32, u32, u64, u64, u64, u64, i32, u64, P32, P64, P64, P64]
         _lib = lib
@@ -140,6 +146,16 @@ class Field:
     def squarefree(self, coeffs):
         c = np.ascontiguousarray(coeffs, dtype=np.int32)
         return bool(self._lib.orc_squarefree(self._h, len(c) - 1, _p32(c)))
+
+    def factor_degrees(self, coeffs):
+        """n[m] = number of irreducible factors of degree m (m = 0..d) of the
+        square-free coeffs (c_0..c_d) over F_q, by distinct-degree
+        factorisation; None if not square-free of degree d."""
+        c = np.ascontiguousarray(coeffs, dtype=np.int32)
+        n = np.zeros(len(c), dtype=np.int32)
+        if self._lib.orc_factor_degrees(self._h, len(c) - 1, _p32(c), _p32(n)) != 0:
+            return None
+        return [int(v) for v in n]
 
 
 def family_size(q: int, kind: int, degree: int, sample_count: int = 0) -> int:
@@ -214,3 +230,158 @@ def cpu_count(g: int, q: int, kind: int, degree: int, first: int, count: int, *,
         raise ValueError(f"hwc_cpu_count failed rc={rc}")
     n = n_e.value
     return counts[:n].copy(), mult[:n].copy(), n_sq.value
+
+
+def lambda_codes(g: int, q: int, kind: int, degree: int, first: int, count: int, *,
+                 seed: int = 0, sample_count: int = 0, threads: int | None = None):
+    """lambda(f) of eq. 1.2 per member (uint64 codes sum_m n_m 16^(m-1), n_m the
+    parts equal to m of the partition of 2g+2; an extra part 1 for degree
+    2g+1; 0 for members that are not square-free)."""
+    lib = _load()
+    if threads is None:
+        threads = os.cpu_count() or 1
+    codes = np.zeros(count, dtype=np.uint64)
+    rc = lib.orc_lambda_codes(g, q, kind, degree, seed, sample_count, first, count, threads,
+                              codes.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+    if rc != 0:
+        raise ValueError(f"oracle lambda failed rc={rc}")
+    return codes
+
+
+def lambda_histogram(g: int, q: int, kind: int, degree: int, first: int, count: int, **kw):
+    """N_{g,q} of eq. 1.2 restricted to members [first, first+count) of a
+    family, weight 1: rows (#C_1..#C_g, lambda code) sorted by lambda code then
+    tuple, and their multiplicities."""
+    counts, sqf = count_polys(g, q, kind, degree, first, count, **kw)
+    codes = lambda_codes(g, q, kind, degree, first, count, seed=kw.get("seed", 0),
+                         sample_count=kw.get("sample_count", 0), threads=kw.get("threads"))
+    sel = sqf.astype(bool)
+    rows = np.concatenate([codes[sel].astype(np.int64)[:, None], counts[sel].astype(np.int64)], axis=1)
+    if rows.shape[0] == 0:
+        return np.zeros((0, g), np.int32), np.zeros(0, np.uint64), np.zeros(0, np.uint64)
+    uniq, mult = np.unique(rows, axis=0, return_counts=True)
+    return uniq[:, 1:].astype(np.int32), uniq[:, 0].astype(np.uint64), mult.astype(np.uint64)
+
+
+def count_list(g: int, q: int, coeffs: np.ndarray, threads: int | None = None):
+    """Point counts, square-freeness and lambda codes of explicit polynomials:
+    coeffs int32 [n, d+1] (c_0..c_d, digits).  Returns (counts int32 [n, g],
+    sqf uint8 [n], codes uint64 [n])."""
+    lib = _load()
+    if threads is None:
+        threads = os.cpu_count() or 1
+    c = np.ascontiguousarray(coeffs, dtype=np.int32)
+    n, d1 = c.shape
+    counts = np.zeros((n, g), np.int32)
+    sqf = np.zeros(n, np.uint8)
+    codes = np.zeros(n, np.uint64)
+    rc = lib.orc_count_list(g, q, d1 - 1, n, _p32(c), threads, _p32(counts),
+                            sqf.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                            codes.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+    if rc != 0:
+        raise ValueError(f"oracle count_list failed rc={rc}")
+    return counts, sqf, codes
+
+
+# ---------------------------------------------------------------------------
+# Reduced families (Sec. 1.2-1.3) and N_{g,q} (eq. 1.2)
+
+def _fq(q: int):
+    return Field(q, 1)
+
+
+def generator_digit(q: int) -> int:
+    """The smallest F_q digit whose powers give all of F_q^x (oracle arithmetic)."""
+    F = _fq(q)
+    for w in range(2, q):
+        x, order = w, 1
+        while x != 1:
+            x = F.fq_mul(x, w)
+            order += 1
+        if order == q - 1:
+            return w
+    return 1   # q = 3: F_3^x = {1, 2}, generated by 2 (reached above); q = 2 not used
+
+
+def reduced_patterns(q: int, d: int):
+    """The support patterns of P'_d for p not dividing d, in index order:
+    ('A',) c_d X^d + 1;  ('B',) c_d X^d + X;  (i, j) for 1 <= i <= d-2,
+    0 <= j < i: c_d X^d + X^i + c_j X^j + c_{j-1} X^(j-1) + ... + c_0 with
+    c_j in R_{i-j} (the coset representatives w^t, t < gcd(q-1, i-j)).
+    Returns [(pattern, members, mult)]: mult = the number of polynomials of
+    degree d whose reduction has the member's pattern, over the members of the
+    pattern counted with their twists: q translations times the free nonzero
+    coefficients, so q (q-1)^2 / (2 (q-1)) = q(q-1)/2 for A and B, and
+    q (q-1)^3 q^j / (2 (q-1) gcd(q-1, i-j) q^j) = q(q-1)^2 / (2 gcd(q-1, i-j))
+    for (i, j).  (The paper lists A and the (i, j) patterns; B, the f whose
+    only coefficients are c_d and c_1 after translation, is missing there.)"""
+    from math import gcd
+    out = [(("A",), q - 1, q * (q - 1) // 2), (("B",), q - 1, q * (q - 1) // 2)]
+    for i in range(1, d - 1):
+        for j in range(i):
+            gg = gcd(q - 1, i - j)
+            out.append(((i, j), (q - 1) * gg * q ** j, q * (q - 1) ** 2 // (2 * gg)))
+    return out
+
+
+def reduced_family(q: int, d: int):
+    """Every member of P'_d (twist folded: the coefficient after the lead is 1)
+    in index order: (coeffs int32 [n, d+1], mult uint64 [n]).  Within a
+    pattern, member index = low digits (c_0 + c_1 q + ... + c_{j-1} q^(j-1))
+    + q^j (t + gcd (c_d - 1)).  Pure Python: small q only."""
+    F = _fq(q)
+    w = generator_digit(q)
+    pw = [1]
+    for _ in range(q):
+        pw.append(F.fq_mul(pw[-1], w))
+    rows, mult = [], []
+    for pat, n, m in reduced_patterns(q, d):
+        for idx in range(n):
+            c = [0] * (d + 1)
+            if pat == ("A",):
+                c[d], c[0] = 1 + idx, 1
+            elif pat == ("B",):
+                c[d], c[1] = 1 + idx, 1
+            else:
+                i, j = pat
+                low = idx % q ** j
+                rest = idx // q ** j
+                from math import gcd
+                gg = gcd(q - 1, i - j)
+                t, cd = rest % gg, 1 + rest // gg
+                for k in range(j):
+                    c[k] = low % q
+                    low //= q
+                c[d], c[i], c[j] = cd, 1, pw[t]
+            rows.append(c)
+            mult.append(m)
+    return np.asarray(rows, np.int32), np.asarray(mult, np.uint64)
+
+
+def n_gq(g: int, q: int, d: int, reduced: bool):
+    """N_{g,q} of eq. 1.2 restricted to degree d, as {(lambda code, a_1..a_g): count}
+    with a_k = q^k + 1 - #C_k (eq. 1.1).
+    reduced=False: every square-free f of degree d (the definition).
+    reduced=True: the members f of P'_d with weight mult(f), each counted for f
+    and for its quadratic twist e f (e a non-square), whose a_k is (-1)^k a_k."""
+    out = {}
+    if reduced:
+        coeffs, mult = reduced_family(q, d)
+        counts, sqf, codes = count_list(g, q, coeffs)
+        for row, s, code, m in zip(counts, sqf, codes, mult):
+            if not s:
+                continue
+            a = tuple(q ** (k + 1) + 1 - int(row[k]) for k in range(g))
+            tw = tuple(v if (k + 1) % 2 == 0 else -v for k, v in enumerate(a))
+            for key in ((int(code),) + a, (int(code),) + tw):
+                out[key] = out.get(key, 0) + int(m)
+        return out
+    size = (q - 1) * q ** d
+    counts, sqf = count_polys(g, q, ALL, d, 0, size)
+    codes = lambda_codes(g, q, ALL, d, 0, size)
+    for row, s, code in zip(counts, sqf, codes):
+        if not s:
+            continue
+        key = (int(code),) + tuple(q ** (k + 1) + 1 - int(row[k]) for k in range(g))
+        out[key] = out.get(key, 0) + 1
+    return out

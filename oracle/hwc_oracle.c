@@ -443,6 +443,125 @@ int orc_squarefree(void *hdl, int d, const int32_t *c)
 }
 
 /* ------------------------------------------------------------------ */
+/* factorisation pattern lambda(f) (Sec. 1.1, eq. 1.2)                  */
+/* by distinct-degree factorisation: for monic square-free f over F_q, */
+/* gcd(f, X^(q^m) - X) is the product of the irreducible factors of    */
+/* f whose degree divides m; removing them degree by degree leaves the */
+/* factors of each exact degree m.                                     */
+
+/* r = a * b mod f over F_q; f monic of degree n, a and b of degree < n */
+static void fqx_mulmod(const orc_field *F, const int *a, const int *b, const int *f, int n, int *r)
+{
+    int q = F->q, t[2 * ORC_MAXD];
+    for (int i = 0; i < 2 * n - 1; ++i) t[i] = 0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            t[i + j] = F->add[t[i + j] * q + F->mul[a[i] * q + b[j]]];
+    for (int i = 2 * n - 2; i >= n; --i) {   /* X^i = X^(i-n) * (X^n - f) */
+        int c = t[i];
+        if (!c) continue;
+        t[i] = 0;
+        for (int j = 0; j < n; ++j) t[i - n + j] = F->add[t[i - n + j] * q + F->neg[F->mul[c * q + f[j]]]];
+    }
+    for (int i = 0; i < n; ++i) r[i] = t[i];
+}
+
+/* degree of a (array of n+1 coefficients), -1 for the zero polynomial */
+static int fqx_deg(const int *a, int n)
+{
+    while (n >= 0 && a[n] == 0) --n;
+    return n;
+}
+
+/* g = gcd(a, b) made monic; a and b are overwritten; returns deg g */
+static int fqx_gcd(const orc_field *F, int *a, int da, int *b, int db, int *g)
+{
+    int q = F->q;
+    da = fqx_deg(a, da);
+    db = fqx_deg(b, db);
+    while (db >= 0) {
+        int il = F->inv[b[db]];
+        for (int t = da; t >= db; --t) {
+            int cf = F->mul[a[t] * q + il];
+            if (!cf) continue;
+            for (int i = 0; i <= db; ++i) a[t - db + i] = F->add[a[t - db + i] * q + F->neg[F->mul[cf * q + b[i]]]];
+        }
+        da = fqx_deg(a, db - 1);
+        int *tp = a; a = b; b = tp;
+        int td = da; da = db; db = td;
+    }
+    if (da < 0) return -1;
+    int il = F->inv[a[da]];
+    for (int i = 0; i <= da; ++i) g[i] = F->mul[a[i] * q + il];
+    return da;
+}
+
+/* a <- a / b (exact division by monic b) */
+static int fqx_divexact(const orc_field *F, int *a, int da, const int *b, int db, int *quo)
+{
+    int q = F->q;
+    for (int i = 0; i <= da - db; ++i) quo[i] = 0;
+    for (int t = da; t >= db; --t) {
+        int c = a[t];
+        quo[t - db] = c;
+        if (!c) continue;
+        for (int i = 0; i <= db; ++i) a[t - db + i] = F->add[a[t - db + i] * q + F->neg[F->mul[c * q + b[i]]]];
+    }
+    return da - db;
+}
+
+/* n_by_deg[m] (m = 0..d) = number of irreducible factors of degree m of the
+ * square-free f = sum c_i X^i of degree d over F_q (F: any field of this
+ * oracle with this q; its F_q tables are used).  Returns 0, -1 if f is not
+ * square-free of degree d. */
+int orc_factor_degrees(void *hdl, int d, const int32_t *c, int32_t *n_by_deg)
+{
+    orc_field *F = (orc_field *)hdl;
+    int q = F->q;
+    if (d < 1 || d > ORC_MAXD || c[d] == 0 || !orc_squarefree(hdl, d, c)) return -1;
+    for (int m = 0; m <= d; ++m) n_by_deg[m] = 0;
+    int f[ORC_MAXD + 1], rest[ORC_MAXD + 1];
+    int il = F->inv[c[d]];
+    for (int i = 0; i <= d; ++i) f[i] = F->mul[c[i] * q + il];   /* monic */
+    memcpy(rest, f, sizeof(int) * (d + 1));
+    int drest = d;
+    /* h = X^(q^m) mod f, by q-th powers of the previous h */
+    int h[ORC_MAXD], x[ORC_MAXD];
+    for (int i = 0; i < d; ++i) h[i] = x[i] = 0;
+    if (d == 1) {
+        n_by_deg[1] = 1;
+        return 0;
+    }
+    h[1] = x[1] = 1;
+    for (int m = 1; 2 * m <= drest; ++m) {
+        int base[ORC_MAXD], acc[ORC_MAXD], t[ORC_MAXD];
+        memcpy(base, h, sizeof(int) * d);
+        for (int i = 0; i < d; ++i) acc[i] = 0;
+        acc[0] = 1;
+        for (long ex = q; ex; ex >>= 1) {
+            if (ex & 1) { fqx_mulmod(F, acc, base, f, d, t); memcpy(acc, t, sizeof(int) * d); }
+            fqx_mulmod(F, base, base, f, d, t);
+            memcpy(base, t, sizeof(int) * d);
+        }
+        memcpy(h, acc, sizeof(int) * d);
+        /* gcd(rest, h - X) */
+        int a[ORC_MAXD + 1], b[ORC_MAXD + 1], g[ORC_MAXD + 1];
+        memcpy(a, rest, sizeof(int) * (drest + 1));
+        for (int i = 0; i < d; ++i) b[i] = F->add[h[i] * q + F->neg[x[i]]];
+        b[d] = 0;
+        int dg = fqx_gcd(F, a, drest, b, d - 1, g);
+        if (dg >= 1) {
+            n_by_deg[m] = dg / m;
+            int quo[ORC_MAXD + 1];
+            drest = fqx_divexact(F, rest, drest, g, dg, quo);
+            memcpy(rest, quo, sizeof(int) * (drest + 1));
+        }
+    }
+    if (drest >= 1) n_by_deg[drest] += 1;   /* what is left is irreducible */
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
 /* families                                                            */
 
 static uint64_t splitmix64_at(uint64_t seed, uint64_t j)
@@ -535,6 +654,87 @@ int orc_count_polys(int g, int q, int kind, int d, uint64_t seed, uint64_t sampl
         }
     }
     for (int k = 1; k <= g; ++k) orc_field_free(F[k]);
+    return 0;
+}
+
+/* Point counts of an explicit list of polynomials: coeffs[i*(d+1) + n] = c_n
+ * of polynomial i (F_q digits, c_d != 0); counts[i*g + k-1] = #C(F_{q^k}),
+ * sqf[i] = square-free, codes[i] = lambda code (as orc_lambda_codes; 0 if
+ * not square-free).  Non-square-free entries get counts 0.  Returns 0, -1
+ * (bad argument), -3 (field). */
+int orc_count_list(int g, int q, int d, uint64_t n, const int32_t *coeffs, int nthreads, int32_t *counts,
+                   uint8_t *sqf, uint64_t *codes)
+{
+    int p, e;
+    if (g < 1 || g > ORC_MAXK || prime_power(q, &p, &e) || d < 1 || d > ORC_MAXD) return -1;
+    orc_field *F[ORC_MAXK + 1];
+    for (int k = 1; k <= g; ++k) {
+        F[k] = (orc_field *)orc_field_new(q, k, 0, 0);
+        if (!F[k]) {
+            for (int j = 1; j < k; ++j) orc_field_free(F[j]);
+            return -3;
+        }
+    }
+    if (nthreads <= 0) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads)
+    for (long i = 0; i < (long)n; ++i) {
+        const int32_t *c = coeffs + i * (d + 1);
+        int32_t nd[ORC_MAXD + 1];
+        int s = c[d] != 0 && orc_squarefree(F[1], d, c);
+        sqf[i] = (uint8_t)s;
+        uint64_t code = 0;
+        if (s && orc_factor_degrees(F[1], d, c, nd) == 0) {
+            if (d == 2 * g + 1) nd[1] += 1;
+            for (int m = 1; m <= d; ++m) code += (uint64_t)nd[m] << (4 * (m - 1));
+        }
+        codes[i] = code;
+        for (int k = 1; k <= g; ++k) {
+            if (!s) { counts[i * g + (k - 1)] = 0; continue; }
+            const orc_field *Fk = F[k];
+            long r0 = 0, rsq = 0;
+            int dx[ORC_MAXK];
+            for (long x = 0; x < Fk->Q; ++x) {
+                fQ_to_digits(Fk, x, dx);
+                long y = eval_d(Fk, d, c, dx);
+                if (y == 0) ++r0;
+                else if (Fk->chi[y] == 1) ++rsq;
+            }
+            int finf = (d == 2 * g + 2) ? c[d] : 0;
+            counts[i * g + (k - 1)] = (int32_t)(r0 + 2 * rsq + (1 + Fk->chi[finf]));
+        }
+    }
+    for (int k = 1; k <= g; ++k) orc_field_free(F[k]);
+    return 0;
+}
+
+/* lambda(f) of eq. 1.2 for members [first, first+count): the partition of
+ * 2g+2 given by the degrees of the irreducible factors of f, with one more
+ * part 1 when deg f = 2g+1; coded as sum_m n_m 16^(m-1), n_m the number of
+ * parts equal to m.  0 for members that are not square-free.  Returns 0, or
+ * -1 / -2 / -3 as orc_count_polys. */
+int orc_lambda_codes(int g, int q, int kind, int d, uint64_t seed, uint64_t sample_count, uint64_t first,
+                     uint64_t count, int nthreads, uint64_t *codes)
+{
+    int p, e;
+    if (g < 1 || g > ORC_MAXK || prime_power(q, &p, &e)) return -1;
+    if (d != 2 * g + 1 && d != 2 * g + 2) return -1;
+    uint64_t n = orc_family_size(q, kind, d, sample_count);
+    if (first > n || count > n - first) return -2;
+    orc_field *F = (orc_field *)orc_field_new(q, 1, 0, 0);
+    if (!F) return -3;
+    if (nthreads <= 0) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads)
+    for (long i = 0; i < (long)count; ++i) {
+        int32_t c[ORC_MAXD + 1], nd[ORC_MAXD + 1];
+        orc_decode(q, kind, d, seed, first + (uint64_t)i, c);
+        uint64_t code = 0;
+        if (orc_factor_degrees(F, d, c, nd) == 0) {
+            if (d == 2 * g + 1) nd[1] += 1;   /* the extra part 1 of odd degree */
+            for (int m = 1; m <= d; ++m) code += (uint64_t)nd[m] << (4 * (m - 1));
+        }
+        codes[i] = code;
+    }
+    orc_field_free(F);
     return 0;
 }
 
