@@ -65,6 +65,23 @@ extern "C" {
 #define HWC_FAM_ALL_DEG 0u
 #define HWC_FAM_MONIC_NOSUB 1u
 #define HWC_FAM_MONIC_NOSUB_SAMPLED 2u
+/*  HWC_FAM_REDUCED       the reduced polynomials P'_d of Sec. 1.2-1.3 (p not
+ *                        dividing d): one polynomial per class of the affine
+ *                        maps X -> aX + b and f -> f / e^2, with the first
+ *                        coefficient below the lead set to 1 (the quadratic
+ *                        twist folded in).  Patterns in this order:
+ *                          A: c_d X^d + 1, B: c_d X^d + X (q-1 members each),
+ *                          (i, j), 1 <= i <= d-2, 0 <= j < i (i outer):
+ *                          c_d X^d + X^i + w^t X^j + c_{j-1} X^(j-1) + ... + c_0,
+ *                          t < gcd(q-1, i-j), w the smallest digit generating
+ *                          F_q^x; (q-1) gcd(q-1, i-j) q^j members, index =
+ *                          c_0 + c_1 q + ... + q^j (t + gcd (c_d - 1)).
+ *                        Each member is counted with weight mult(f) (q(q-1)/2
+ *                        for A and B, q(q-1)^2 / (2 gcd(q-1, i-j)) for (i, j))
+ *                        twice: with its own (a_1..a_g) and with its twist's,
+ *                        a_k -> (-1)^k a_k.  The histogram then equals the one
+ *                        over every square-free f of degree d (eq. 1.2). */
+#define HWC_FAM_REDUCED 3u
 
 typedef struct {
     uint32_t kind;          /* HWC_FAM_*                                   */
@@ -276,6 +293,25 @@ int hwc_serve_latency(hwc_server_t *s, uint64_t ticket, double *queued_us,
                       double *total_us);
 /* Stop the thread (finishing the active step) and free everything. */
 int hwc_serve_close(hwc_server_t *s);
+
+/* ------------------------------------------------------------------ */
+/* Single curves (Sec. 4, Table 1: one curve counted over F_{p^2})     */
+
+#define HWC_MAX_Q_CURVE (1u << 24)   /* largest F_{q^k} for hwc_curve_count */
+
+/* #C_f(F_{q^k}) of explicit curves y^2 = f_i(x), i < n: coeffs[i*(d+1) + j]
+ * is the F_q digit c_j of f_i (c_d != 0), counts[i] receives
+ * r^0 + 2 r^sq + 1 + chi(f(inf)) as in Sec. 1.1 (f need not be
+ * square-free).  The points are spread over the whole GPU: every field
+ * F_{q^m}, m | k, evaluates one point per Frobenius orbit of its elements of
+ * exact degree m, with Zech tables of up to HWC_MAX_Q_CURVE elements read
+ * from global memory (L2-resident); the tables are built on first use and
+ * cached.  1 <= d <= 10; coeffs and counts are HOST arrays.  Synchronous on
+ * `stream`.  Errors: HWC_ERR_ARG, HWC_ERR_TOO_LARGE (q^k above
+ * HWC_MAX_Q_CURVE), HWC_ERR_NOMEM, HWC_ERR_CUDA.  If ms is not NULL it
+ * receives the device time of the count kernels (CUDA events). */
+int hwc_curve_count(uint32_t q, uint32_t k, uint32_t d, uint64_t n, const uint32_t *coeffs, int64_t *counts,
+                    void *stream, float *ms);
 
 /* ------------------------------------------------------------------ */
 /* Counting without device allocation                                  */

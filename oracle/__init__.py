@@ -364,18 +364,29 @@ def n_gq(g: int, q: int, d: int, reduced: bool):
     reduced=False: every square-free f of degree d (the definition).
     reduced=True: the members f of P'_d with weight mult(f), each counted for f
     and for its quadratic twist e f (e a non-square), whose a_k is (-1)^k a_k."""
-    out = {}
+    qk = np.array([q ** (k + 1) + 1 for k in range(g)], np.int64)
     if reduced:
         coeffs, mult = reduced_family(q, d)
         counts, sqf, codes = count_list(g, q, coeffs)
-        for row, s, code, m in zip(counts, sqf, codes, mult):
-            if not s:
-                continue
-            a = tuple(q ** (k + 1) + 1 - int(row[k]) for k in range(g))
-            tw = tuple(v if (k + 1) % 2 == 0 else -v for k, v in enumerate(a))
-            for key in ((int(code),) + a, (int(code),) + tw):
-                out[key] = out.get(key, 0) + int(m)
-        return out
+        sel = sqf.astype(bool)
+        a = qk[None, :] - counts[sel].astype(np.int64)
+        sign = np.array([-1 if (k + 1) % 2 else 1 for k in range(g)], np.int64)
+        rows = np.concatenate([np.concatenate([codes[sel].astype(np.int64)[:, None], a], axis=1),
+                               np.concatenate([codes[sel].astype(np.int64)[:, None], a * sign], axis=1)])
+        w = np.concatenate([mult[sel], mult[sel]]).astype(np.int64)
+    else:
+        size = (q - 1) * q ** d
+        counts, sqf = count_polys(g, q, ALL, d, 0, size)
+        codes = lambda_codes(g, q, ALL, d, 0, size)
+        sel = sqf.astype(bool)
+        rows = np.concatenate([codes[sel].astype(np.int64)[:, None], qk[None, :] - counts[sel].astype(np.int64)],
+                              axis=1)
+        w = np.ones(rows.shape[0], np.int64)
+    if rows.shape[0] == 0:
+        return {}
+    uniq, inv = np.unique(rows, axis=0, return_inverse=True)
+    tot = np.bincount(inv.reshape(-1), weights=w.astype(np.float64), minlength=len(uniq))
+    return {tuple(int(v) for v in r): int(round(t)) for r, t in zip(uniq, tot)}
     size = (q - 1) * q ** d
     counts, sqf = count_polys(g, q, ALL, d, 0, size)
     codes = lambda_codes(g, q, ALL, d, 0, size)
@@ -385,3 +396,29 @@ def n_gq(g: int, q: int, d: int, reduced: bool):
         key = (int(code),) + tuple(q ** (k + 1) + 1 - int(row[k]) for k in range(g))
         out[key] = out.get(key, 0) + 1
     return out
+
+
+def curve_count(q: int, k: int, coeffs) -> np.ndarray:
+    """#C(F_{q^k}) of explicit curves y^2 = f(x) (coeffs [n, d+1], digits),
+    square-free or not: the count of Sec. 1.1 over every x of F_{q^k}."""
+    c = np.ascontiguousarray(np.atleast_2d(coeffs), dtype=np.int32)
+    counts, _, _ = count_list_unfiltered(k, q, c)
+    return counts[:, k - 1].astype(np.int64)
+
+
+def count_list_unfiltered(g: int, q: int, coeffs: np.ndarray, threads: int | None = None):
+    """count_list with every polynomial evaluated (square-free or not)."""
+    lib = _load()
+    if threads is None:
+        threads = os.cpu_count() or 1
+    c = np.ascontiguousarray(coeffs, dtype=np.int32)
+    n, d1 = c.shape
+    counts = np.zeros((n, g), np.int32)
+    sqf = np.zeros(n, np.uint8)
+    codes = np.zeros(n, np.uint64)
+    rc = lib.orc_count_list(g, q, d1 - 1, n, _p32(c), -threads, _p32(counts),
+                            sqf.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                            codes.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+    if rc != 0:
+        raise ValueError(f"oracle count_list failed rc={rc}")
+    return counts, sqf, codes

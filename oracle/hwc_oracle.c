@@ -46,7 +46,7 @@
 #define ORC_MAXE 16
 #define ORC_MAXK 4
 #define ORC_MAXD 10
-#define ORC_MAXQ (1L << 22)
+#define ORC_MAXQ (1L << 24)
 
 enum { ORC_ALL = 0, ORC_MZ = 1, ORC_MZ_SAMP = 2 };
 
@@ -660,8 +660,9 @@ int orc_count_polys(int g, int q, int kind, int d, uint64_t seed, uint64_t sampl
 /* Point counts of an explicit list of polynomials: coeffs[i*(d+1) + n] = c_n
  * of polynomial i (F_q digits, c_d != 0); counts[i*g + k-1] = #C(F_{q^k}),
  * sqf[i] = square-free, codes[i] = lambda code (as orc_lambda_codes; 0 if
- * not square-free).  Non-square-free entries get counts 0.  Returns 0, -1
- * (bad argument), -3 (field). */
+ * not square-free).  Non-square-free entries get counts 0, unless nthreads is
+ * negative (then every entry is counted, with -nthreads threads).  Returns 0,
+ * -1 (bad argument), -3 (field). */
 int orc_count_list(int g, int q, int d, uint64_t n, const int32_t *coeffs, int nthreads, int32_t *counts,
                    uint8_t *sqf, uint64_t *codes)
 {
@@ -675,7 +676,9 @@ int orc_count_list(int g, int q, int d, uint64_t n, const int32_t *coeffs, int n
             return -3;
         }
     }
-    if (nthreads <= 0) nthreads = 1;
+    const int all = nthreads < 0;
+    if (nthreads < 0) nthreads = -nthreads;
+    if (nthreads == 0) nthreads = 1;
 #pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads)
     for (long i = 0; i < (long)n; ++i) {
         const int32_t *c = coeffs + i * (d + 1);
@@ -689,7 +692,7 @@ int orc_count_list(int g, int q, int d, uint64_t n, const int32_t *coeffs, int n
         }
         codes[i] = code;
         for (int k = 1; k <= g; ++k) {
-            if (!s) { counts[i * g + (k - 1)] = 0; continue; }
+            if (!s && !all) { counts[i * g + (k - 1)] = 0; continue; }
             const orc_field *Fk = F[k];
             long r0 = 0, rsq = 0;
             int dx[ORC_MAXK];
@@ -699,7 +702,8 @@ int orc_count_list(int g, int q, int d, uint64_t n, const int32_t *coeffs, int n
                 if (y == 0) ++r0;
                 else if (Fk->chi[y] == 1) ++rsq;
             }
-            int finf = (d == 2 * g + 2) ? c[d] : 0;
+            /* points at infinity: one for odd degree, 1 + chi(c_d) for even degree */
+            int finf = (d % 2 == 0) ? c[d] : 0;
             counts[i * g + (k - 1)] = (int32_t)(r0 + 2 * rsq + (1 + Fk->chi[finf]));
         }
     }

@@ -71,11 +71,51 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t j)
 // ---------------------------------------------------------------------
 // member decoding (the choice of f in Algorithm 1; family definitions in hwc.h)
 
+// member idx of the reduced family (HWC_FAM_REDUCED): pattern by its start
+// index, then the digits; returns the pattern
+template <int D>
+__device__ __forceinline__ uint32_t decode_reduced(const KJob &J, uint64_t idx, uint32_t (&c)[D + 1])
+{
+    uint32_t pt = 0;
+    while (pt + 1 < J.red_n && J.red_start[pt + 1] <= idx) ++pt;
+    uint64_t r = idx - J.red_start[pt];
+    const uint32_t q = J.q;
+#pragma unroll
+    for (int i = 0; i <= D; ++i) c[i] = 0;
+    const uint32_t pi = J.red_i[pt], pj = J.red_j[pt];
+    if (pi >= 0xFE) {   // A: c_d X^d + 1, B: c_d X^d + X
+        c[D] = 1 + (uint32_t)r;
+        if (pi == 0xFF) c[0] = 1;
+        else c[1] = 1;
+        return pt;
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+        if ((uint32_t)i < pj) {
+            c[i] = (uint32_t)(r % q);
+            r /= q;
+        }
+    const uint32_t gg = J.red_gcd[pt];
+    const uint32_t t = (uint32_t)(r % gg);
+    c[D] = 1 + (uint32_t)(r / gg);
+    const uint32_t w = J.red_w[t];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {   // static indices: c stays in registers
+        if ((uint32_t)i == pi) c[i] = 1;
+        if ((uint32_t)i == pj) c[i] = w;
+    }
+    return pt;
+}
+
 template <int D>
 __device__ __forceinline__ void decode_member(const KJob &J, uint64_t m, uint32_t (&c)[D + 1])
 {
     uint64_t idx = J.first + m;
     uint32_t kind = J.kind;
+    if (kind == HWC_FAM_REDUCED) {
+        decode_reduced<D>(J, idx, c);
+        return;
+    }
     if (kind == HWC_FAM_MONIC_NOSUB_SAMPLED) {
         idx = __umul64hi(splitmix64_at(J.seed, idx), J.fam_mz);
         kind = HWC_FAM_MONIC_NOSUB;
@@ -262,14 +302,14 @@ __device__ __forceinline__ uint32_t chain_step(uint32_t z, uint32_t d, uint32_t 
 // ---------------------------------------------------------------------
 // histogram
 
-__device__ __forceinline__ void hist_insert(const KJob &J, unsigned long long key, uint32_t cnt)
+__device__ __forceinline__ void hist_insert(const KJob &J, unsigned long long key, unsigned long long cnt)
 {
     uint32_t h = (uint32_t)mix64(key) & J.hmask;
     for (uint32_t probe = 0; probe <= J.hmask; ++probe) {
         unsigned long long cur = *((volatile unsigned long long *)&J.hkeys[h]);
         if (cur == kEmptyKey) cur = atomicCAS(&J.hkeys[h], kEmptyKey, key);
         if (cur == kEmptyKey || cur == key) {
-            atomicAdd(&J.hcounts[h], (unsigned long long)cnt);
+            atomicAdd(&J.hcounts[h], cnt);
             return;
         }
         h = (h + 1) & J.hmask;
@@ -278,7 +318,8 @@ __device__ __forceinline__ void hist_insert(const KJob &J, unsigned long long ke
 }
 
 struct WarpStats {
-    uint32_t examined = 0, sqf = 0;
+    uint32_t examined = 0;
+    unsigned long long sqf = 0;   // square-free members (weighted for reduced families)
 };
 
 // S_k = sum over x in F_{q^k} of chi_{q^k}(f(x)) from the sums of the fields'

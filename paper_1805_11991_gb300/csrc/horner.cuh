@@ -160,7 +160,14 @@ __device__ __forceinline__ void process_tile(const KJob &J, uint64_t tile, const
 #pragma unroll
     for (int i = 0; i <= D; ++i) c[i] = 0;
     c[D] = 1;
-    if (valid) decode_member<D>(J, m, c);
+    // reduced families: weight mult(f) of the member's pattern, counted for f
+    // and for its quadratic twist
+    const bool reduced = J.kind == HWC_FAM_REDUCED;
+    unsigned long long wgt = 1;
+    if (valid) {
+        if (reduced) wgt = J.red_mult[decode_reduced<D>(J, J.first + m, c)];
+        else decode_member<D>(J, m, c);
+    }
 
     const uint16_t *s16 = reinterpret_cast<const uint16_t *>(smem);
     const uint32_t *s32 = reinterpret_cast<const uint32_t *>(smem);
@@ -183,7 +190,15 @@ __device__ __forceinline__ void process_tile(const KJob &J, uint64_t tile, const
     }
     const unsigned vmask = __ballot_sync(kFull, valid);
     const unsigned smask = __ballot_sync(kFull, sqf);
-    if (lane == 0) {
+    if (reduced) {   // weighted square-free count: 2 mult(f) per member (f and its twist)
+        unsigned long long ws = sqf ? 2 * wgt : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ws += __shfl_xor_sync(kFull, ws, o);
+        if (lane == 0) {
+            st.examined += __popc(vmask);
+            st.sqf += ws;
+        }
+    } else if (lane == 0) {
         st.examined += __popc(vmask);
         st.sqf += __popc(smask);
     }
@@ -256,7 +271,7 @@ __device__ __forceinline__ void process_tile(const KJob &J, uint64_t tile, const
         }
         return;
     }
-    unsigned long long key = 0;
+    unsigned long long key = 0, tkey = 0;   // tkey: the quadratic twist, a_k -> (-1)^k a_k
     if (J.lam_mode) {
         // (a_1..a_g, lambda(f)) of eq. 1.2: the orbit zeros of exact degree m are
         // the irreducible factors of degree m; what is left is one factor, or two
@@ -286,15 +301,27 @@ __device__ __forceinline__ void process_tile(const KJob &J, uint64_t tile, const
 #pragma unroll
         for (int k = 0; k < G; ++k) {
             const int a = (int)J.Q[k] + 1 - myN[k];   // eq. 1.1
+            const int at = (k & 1) ? a : -a;
             key |= (unsigned long long)(uint32_t)(a + J.key_bias[k]) << J.key_shift[k];
+            tkey |= (unsigned long long)(uint32_t)(at + J.key_bias[k]) << J.key_shift[k];
         }
         key |= lam << J.lam_shift;
+        tkey |= lam << J.lam_shift;
     } else {
 #pragma unroll
         for (int k = 0; k < G; ++k) {
             const int a = (int)J.Q[k] + 1 - myN[k];   // eq. 1.1
+            const int at = (k & 1) ? a : -a;
             key |= (unsigned long long)((uint32_t)(a + 32768) & 0xFFFFu) << (16 * k);
+            tkey |= (unsigned long long)((uint32_t)(at + 32768) & 0xFFFFu) << (16 * k);
         }
+    }
+    if (reduced) {
+        if (sqf) {
+            hist_insert(J, key, wgt);
+            hist_insert(J, tkey, wgt);
+        }
+        return;
     }
     if (sqf) {
         const unsigned peers = __match_any_sync(smask, key);

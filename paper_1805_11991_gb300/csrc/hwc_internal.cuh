@@ -18,7 +18,7 @@ namespace hwc {
 
 constexpr int kMaxG = 4;
 constexpr int kMaxD = 2 * kMaxG + 2;        // degree 2g+2
-constexpr int kMaxN = 12;                   // degree of F_Q over F_p (Q <= 2^18)
+constexpr int kMaxN = 16;                   // degree of F_Q over F_p (Q <= 2^24)
 constexpr int kMaxE = 8;                    // degree of F_q over F_p
 constexpr uint32_t kWideTable = 0xFFFFFFFFu; // table read from global memory
 constexpr unsigned long long kEmptyKey = ~0ull;
@@ -91,12 +91,12 @@ enum TabKind : uint32_t {
     kTab17Smem = 3,       // d_z17lo / d_z17hi staged in shared memory (per-member kernel)
 };
 
-int tables_build(uint32_t q, uint32_t k, Tables **out);
+int tables_build(uint32_t q, uint32_t k, Tables **out, uint64_t max_q = HWC_MAX_Q);
 // one point per Frobenius orbit of the elements of exact degree k (host)
 std::vector<uint32_t> orbit_reps(uint32_t q, uint32_t k, uint32_t L);
 void tables_destroy(Tables *t);
 // process-wide cache of tables per (device, q, k); never freed before exit
-int tables_cached(uint32_t q, uint32_t k, const Tables **out);
+int tables_cached(uint32_t q, uint32_t k, const Tables **out, uint64_t max_q = HWC_MAX_Q);
 
 // factor q = p^e, p odd prime
 bool prime_power(uint32_t q, uint32_t *p, uint32_t *e);
@@ -136,6 +136,16 @@ struct KJob {
     uint32_t key_shift[kMaxG];
     int32_t key_bias[kMaxG];
     uint32_t lam_shift;
+    // HWC_FAM_REDUCED: patterns A, B, (i, j) in index order (red_n of them),
+    // red_start[] their first member index (red_start[red_n] = family size),
+    // red_i / red_j the pattern (A: i = 0xFF, B: i = 0xFE), red_gcd, red_mult
+    // the weight, red_w[t] the digit w^t
+    static constexpr int kMaxPat = 2 + (2 * kMaxG) * (2 * kMaxG + 1) / 2;
+    uint32_t red_n;
+    uint64_t red_start[kMaxPat + 1];
+    uint8_t red_i[kMaxPat], red_j[kMaxPat], red_gcd[kMaxPat];
+    uint64_t red_mult[kMaxPat];
+    uint32_t red_w[2 * kMaxG];
     uint32_t smem_u16;                // u16 words of zech2 tables staged in smem
     uint32_t smem_bytes;              // total dynamic smem for this job
     // c_0 fan-out (method 1): groups of q members that differ only in c_0

@@ -63,6 +63,18 @@ static int family_size(uint32_t q, const hwc_family_t *fam, uint64_t *n)
         if (!upow(q, d - 1, &v)) return set_error(HWC_ERR_TOO_LARGE, "family size overflows");
         v = fam->sample_count;
         break;
+    case HWC_FAM_REDUCED: {   // patterns A, B and (i, j) of Sec. 1.2 (see hwc.h)
+        if (d % p == 0) return set_error(HWC_ERR_ARG, "reduced family needs p=%u not dividing d=%u", p, d);
+        v = 2ull * (q - 1);
+        for (uint32_t i = 1; i + 2 <= d; ++i)
+            for (uint32_t j = 0; j < i; ++j) {
+                uint64_t t;
+                if (!upow(q, j, &t) || !mul_ok(t, (uint64_t)(q - 1) * std::gcd(q - 1, i - j), &t) || v + t < v)
+                    return set_error(HWC_ERR_TOO_LARGE, "family size overflows");
+                v += t;
+            }
+        break;
+    }
     default:
         return set_error(HWC_ERR_ARG, "unknown family kind %u", fam->kind);
     }
@@ -258,6 +270,7 @@ struct HostJob {
     KJob kj;
     uint64_t fam_n;
     int warps = 0;   // tuned warps per CTA (two-level kernel)
+    int block = 0;   // threads per CTA of the job's launch when it runs alone
 };
 
 void set_points(KJob &kj, uint32_t k, const Tables *t, bool orbits)
@@ -274,6 +287,47 @@ void set_points(KJob &kj, uint32_t k, const Tables *t, bool orbits)
         while ((1u << s) <= 2 * kj.npts[k - 1] + kj.d) ++s;
         kj.zshift[k - 1] = s;
     }
+}
+
+// the pattern table of the reduced family (HWC_FAM_REDUCED, hwc.h): starts,
+// patterns, gcd(q-1, i-j), mult, and the digits w^t of the smallest digit w
+// generating F_q^x (read off the logs of the digits in F_q)
+static int fill_reduced(KJob &kj, const Tables *t1)
+{
+    const uint32_t q = kj.q, d = kj.d;
+    std::vector<uint32_t> lg(q);
+    HWC_CUDA_TRY(cudaMemcpy(lg.data(), t1->d_coef_log, q * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    const uint32_t L = q - 1;
+    uint32_t w = 1;
+    for (uint32_t c = 2; c < q; ++c)
+        if (lg[c] < L && std::gcd(lg[c], L) == 1) { w = c; break; }
+    std::vector<uint32_t> digit_of_log(L, 0);
+    for (uint32_t c = 1; c < q; ++c) digit_of_log[lg[c] % L] = c;
+    for (uint32_t t = 0; t < 2 * (uint32_t)kMaxG; ++t) kj.red_w[t] = digit_of_log[(uint64_t)t * lg[w] % L];
+    uint32_t n = 0;
+    uint64_t start = 0;
+    const uint64_t m1 = (uint64_t)q * (q - 1) / 2;
+    auto add = [&](uint32_t i, uint32_t j, uint32_t gg, uint64_t size, uint64_t mult) {
+        kj.red_start[n] = start;
+        kj.red_i[n] = (uint8_t)i;
+        kj.red_j[n] = (uint8_t)j;
+        kj.red_gcd[n] = (uint8_t)gg;
+        kj.red_mult[n] = mult;
+        start += size;
+        ++n;
+    };
+    add(0xFF, 0, 1, q - 1, m1);   // A: c_d X^d + 1
+    add(0xFE, 0, 1, q - 1, m1);   // B: c_d X^d + X
+    for (uint32_t i = 1; i + 2 <= d; ++i)
+        for (uint32_t j = 0; j < i; ++j) {
+            const uint32_t gg = std::gcd(q - 1, i - j);
+            uint64_t qj = 1;
+            for (uint32_t e = 0; e < j; ++e) qj *= q;
+            add(i, j, gg, (uint64_t)(q - 1) * gg * qj, (uint64_t)q * (q - 1) * (q - 1) / (2 * gg));
+        }
+    kj.red_n = n;
+    kj.red_start[n] = start;
+    return HWC_OK;
 }
 
 int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n, uint32_t flags, const TuneChoice *tc)
@@ -314,7 +368,8 @@ int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n, uint32_t flags, co
         if (off + 4 * jb.g + 1 > 63) return set_error(HWC_ERR_TOO_LARGE, "lambda key needs %u bits", off + 4 * jb.g + 1);
     }
     // enumerated families with q <= 63: groups of q members share all but c_0
-    const bool fan = !(flags & (HWC_FLAG_HORNER | HWC_FLAG_LAMBDA)) && jb.family.kind != HWC_FAM_MONIC_NOSUB_SAMPLED && jb.q <= 63 &&
+    const bool fan = !(flags & (HWC_FLAG_HORNER | HWC_FLAG_LAMBDA)) && jb.family.kind != HWC_FAM_MONIC_NOSUB_SAMPLED &&
+                     jb.family.kind != HWC_FAM_REDUCED && jb.q <= 63 &&
                      !(tc && tc->method == 0);
     const bool no_triple = tc && tc->no_triple;
     // (method chosen below: two-level fan-out for q <= 31, one-level up to 63,
@@ -341,6 +396,7 @@ int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n, uint32_t flags, co
         }
         kj.zdig[k - 1] = t->d_zdig;
         if (k == 2) kj.coord2 = t->d_coord2;
+        if (k == 1 && jb.family.kind == HWC_FAM_REDUCED && (rc = fill_reduced(kj, t))) return rc;
         // ceil(2^32 / s) recovers l / s exactly for multiples l of s = L/(q-1) < 2^32;
         // s = 1 (k = 1) is encoded as 0
         const uint32_t sdiv = t->L / (jb.q - 1);
@@ -480,6 +536,7 @@ hwc_hist *hwc::hist_from_keys(const KJob &kj, const unsigned long long *keys,
 struct BatchGroup {
     int D = 0;
     uint32_t method = 0, words = 0;
+    int block = 0;                   // the jobs' own block size (one launch per block size)
     int warps = 0;                   // tuned warps per CTA (two-level kernel)
     uint64_t warps_tiles = 0;        // groups of the job that set `warps`
     uint32_t first = 0, n = 0;       // jobs[first .. first+n) (sorted by degree)
@@ -667,12 +724,25 @@ static int batch_create_impl(const hwc_job_t *jobs, size_t n, uint32_t flags, ui
         rc = fill_kjob(jobs[i], filled[i].kj, &filled[i].fam_n, flags, &tc);
         if (rc) { batch_release(b); return rc; }
         filled[i].warps = tc.warps;
+        // the block size this job would launch with alone: jobs that prefer
+        // different blocks get launches of their own (run side by side)
+        const KJob &k = filled[i].kj;
+        LaunchShape sh;
+        uint32_t smem = k.smem_bytes;
+        if (k.method == 2) {
+            const Fan2Need need{k.warp_off, k.warp_bytes};
+            rc = choose_shape_fan2((int)k.d, &need, 1, &sh, &smem, tc.warps);
+        } else {
+            rc = choose_shape((int)k.d, k.method, k.words, k.smem_bytes, true, &sh);
+        }
+        if (rc) { batch_release(b); return rc; }
+        filled[i].block = sh.block;
     }
     std::vector<size_t> order(n);
     std::iota(order.begin(), order.end(), 0);
     auto gkey = [&](size_t x) {
         const KJob &k = filled[x].kj;
-        return std::make_tuple(k.d, k.method, k.words);
+        return std::make_tuple(k.d, k.method, k.words, filled[x].block);
     };
     // within a launch the queue hands out the jobs' work items in this order:
     // the costliest items first (point evaluations per tile), so that the
@@ -706,11 +776,13 @@ static int batch_create_impl(const hwc_job_t *jobs, size_t n, uint32_t flags, ui
         }
         // plain runs: every job is a group of its own (one launch per job)
         if (b->groups.empty() || (flags & HWC_FLAG_PLAIN) || b->groups.back().D != (int)kj.d ||
-            b->groups.back().method != kj.method || b->groups.back().words != kj.words) {
+            b->groups.back().method != kj.method || b->groups.back().words != kj.words ||
+            b->groups.back().block != hj.block) {
             BatchGroup G;
             G.D = (int)kj.d;
             G.method = kj.method;
             G.words = kj.words;
+            G.block = hj.block;
             G.first = (uint32_t)r;
             b->groups.push_back(G);
         }

@@ -514,7 +514,7 @@ void tables_destroy(Tables *t)
     delete t;
 }
 
-int tables_build(uint32_t q, uint32_t k, Tables **out)
+int tables_build(uint32_t q, uint32_t k, Tables **out, uint64_t max_q)
 {
     *out = nullptr;
     uint32_t p, e;
@@ -522,7 +522,8 @@ int tables_build(uint32_t q, uint32_t k, Tables **out)
     if (k < 1 || k > kMaxG) return set_error(HWC_ERR_ARG, "k=%u outside [1,%d]", k, kMaxG);
     uint64_t Q = 1;
     for (uint32_t i = 0; i < k; ++i) Q *= q;
-    if (Q > HWC_MAX_Q) return set_error(HWC_ERR_TOO_LARGE, "Q=q^k=%llu above %u", (unsigned long long)Q, HWC_MAX_Q);
+    if (Q > max_q) return set_error(HWC_ERR_TOO_LARGE, "Q=q^k=%llu above %llu", (unsigned long long)Q,
+                                    (unsigned long long)max_q);
     if (e > (uint32_t)kMaxE || e * k > (uint32_t)kMaxN)
         return set_error(HWC_ERR_TOO_LARGE, "degree e*k=%u too large", e * k);
 
@@ -669,7 +670,7 @@ int tables_build(uint32_t q, uint32_t k, Tables **out)
     return HWC_OK;
 }
 
-int tables_cached(uint32_t q, uint32_t k, const Tables **out)
+int tables_cached(uint32_t q, uint32_t k, const Tables **out, uint64_t max_q)
 {
     static std::mutex mu;
     static std::map<std::tuple<int, uint32_t, uint32_t>, Tables *> cache;
@@ -683,7 +684,7 @@ int tables_cached(uint32_t q, uint32_t k, const Tables **out)
         return HWC_OK;
     }
     Tables *t = nullptr;
-    int rc = tables_build(q, k, &t);
+    int rc = tables_build(q, k, &t, max_q);
     if (rc != HWC_OK) return rc;
     cache[key] = t;
     *out = t;

@@ -19,7 +19,7 @@ OK = 0
 ERR_ARG, ERR_RANGE, ERR_TOO_LARGE, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_BUSY, ERR_STATE = range(-1, -9, -1)
 MAX_Q = 262144
 
-FAM_ALL_DEG, FAM_MONIC_NOSUB, FAM_MONIC_NOSUB_SAMPLED = 0, 1, 2
+FAM_ALL_DEG, FAM_MONIC_NOSUB, FAM_MONIC_NOSUB_SAMPLED, FAM_REDUCED = 0, 1, 2, 3
 FLAG_PLAIN, FLAG_GRAPH, FLAG_HORNER, FLAG_NO_TUNE, FLAG_TIMING, FLAG_FAN1 = 0x1, 0x2, 0x4, 0x8, 0x10, 0x20
 FLAG_ALL_POINTS = 0x40
 FLAG_LAMBDA = 0x80
@@ -102,6 +102,7 @@ def load(build_if_missing: bool = True):
             "hwc_serve_close": (c_int, [vp]),
             "hwc_probe_smem_gather": (c_int, [u32, u32, P(ctypes.c_double)]),
             "hwc_count_noalloc": (c_int, [u32, u32, P(Family), u64, u64, P(vp), u64, vp, vp, vp, vp]),
+            "hwc_curve_count": (c_int, [u32, u32, u32, u64, P(u32), P(ctypes.c_int64), vp, P(ctypes.c_float)]),
         }
         for name, (res, args) in sigs.items():
             f = getattr(lib, name)
@@ -320,6 +321,20 @@ def count_noalloc(g: int, q: int, fam: Family, first: int, n: int, tables, max_e
     handles = (ctypes.c_void_p * len(tables))(*[t._h.value for t in tables])
     _check(_lib.hwc_count_noalloc(g, q, ctypes.byref(fam), first, n, handles, max_entries,
                                   d_counts, d_mult, d_n_out, _stream_ptr(stream)))
+
+
+def curve_count(q: int, k: int, coeffs, stream=None):
+    """hwc_curve_count: #C(F_{q^k}) of explicit curves; coeffs int [n, d+1]
+    (c_0..c_d digits).  Returns (counts int64 [n], device ms of the count)."""
+    load()
+    c = np.ascontiguousarray(np.atleast_2d(coeffs), dtype=np.uint32)
+    n, d1 = c.shape
+    counts = np.zeros(n, np.int64)
+    ms = ctypes.c_float()
+    _check(_lib.hwc_curve_count(q, k, d1 - 1, n, c.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _stream_ptr(stream),
+                                ctypes.byref(ms)))
+    return counts, ms.value
 
 
 def probe_smem_gather(entries: int, iters: int = 4096) -> float:
