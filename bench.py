@@ -17,7 +17,9 @@ At one GPU the line also carries, each with its own device times:
             2^24 sampled members over F_293), batched against plain;
   config2 = g=2, q = 31 and 27, batched;
   served  = configuration 2 as Poisson-timed requests through the server
-            (p50/p99 latency, results against the batched histograms).
+            (p50/p99 latency, results against the batched histograms);
+  table1  = the paper's Table 1 workload: one curve over F_{p^2}, p = 101..3001
+            (hwc_curve_count), beside the paper's times.
 Under torchrun (N > 1) every job's member range is split across the ranks
 (contiguous shards, no collective on the data path) and the shards'
 histograms are gathered and merged after the timed region.
@@ -59,6 +61,8 @@ def parse():
     ap.add_argument("--extra-steps", type=int, default=2,
                     help="timed steps of the config3 extra (batched and plain each)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the autotuner (default kernel choices; no probe launches): for profiles")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--serve", action="store_true",
                     help="also run the served form: the workload cut into requests on a Poisson schedule")
@@ -412,6 +416,37 @@ def extra_workload(hwc, name, steps, warmup, stream, flush, plain=True):
     return out, jobs, results
 
 
+# Sec. 4, Table 1: the curve y^2 = 12x^6 + 13x^5 + 10x^4 + 11x^3 + 16x^2 + 12x + 17
+# over F_{p^2}; the paper's times (ms) on a Tesla K80 and one Xeon E5-2683 core:
+# (p, tables, CPU, GPU eval, GPU reduce)
+TABLE1 = [(101, 4.70, 0.63, 0.36, 0.10), (211, 23.8, 4.47, 1.47, 0.15), (307, 54.9, 12.1, 3.11, 0.22),
+          (401, 99.2, 22.2, 0.95, 0.35), (503, 167, 36.3, 1.25, 0.83), (1009, 892, 148, 2.93, 6.49),
+          (1511, 2545, 349, 394, 19.7), (2003, 5093, 789, 11.5, 36.1), (3001, 13474, 3669, 15.4, 82.6)]
+TABLE1_CURVE = [17, 12, 16, 11, 10, 13, 12]   # c_0..c_6
+
+
+def table1_leg(hwc, reps=5):
+    """The paper's only timed workload: one curve over F_{p^2} per p of Table 1,
+    through hwc_curve_count (tables built on the first call, then cached).
+    Reports the table build (wall clock of the first call minus its count),
+    the count's device time (best of `reps`, CUDA events) and evals/s = p^2 / t,
+    beside the paper's K80 times (context: other hardware, one curve)."""
+    import numpy as np
+    c = np.array([TABLE1_CURVE])
+    hwc.curve_count(3, 2, np.array([[1, 0, 0, 0, 0, 0, 1]]))   # load the kernels
+    rows = []
+    for p, tab, cpu, ev, red in TABLE1:
+        t0 = time.perf_counter()
+        cnt, ms0 = hwc.curve_count(p, 2, c)
+        first_ms = 1e3 * (time.perf_counter() - t0)
+        best = min(hwc.curve_count(p, 2, c)[1] for _ in range(reps))
+        rows.append({"p": p, "count": int(cnt[0]), "tables_ms": max(0.0, first_ms - ms0), "count_ms": best,
+                     "evals_per_s": p * p / (best * 1e-3), "paper_tables_ms": tab, "paper_cpu_ms": cpu,
+                     "paper_gpu_eval_reduce_ms": ev + red,
+                     "vs_paper_gpu": (ev + red) / best})
+    return rows
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -437,8 +472,9 @@ def main():
         a, n = shard.shard_range(s.first, s.n(), rank, world)
         jobs.append(s.with_range(a, n))
     hjobs = _hjobs(hwc, jobs)
-    batched = hwc.Batch(hjobs, flags=hwc.FLAG_GRAPH | hwc.FLAG_TIMING)
-    plain = hwc.Batch(hjobs, flags=hwc.FLAG_PLAIN | hwc.FLAG_TIMING)
+    tune = hwc.FLAG_NO_TUNE if args.no_tune else 0
+    batched = hwc.Batch(hjobs, flags=hwc.FLAG_GRAPH | hwc.FLAG_TIMING | tune)
+    plain = hwc.Batch(hjobs, flags=hwc.FLAG_PLAIN | hwc.FLAG_TIMING | tune)
     stream = torch.cuda.Stream()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
 
@@ -547,6 +583,7 @@ def main():
         line["served"] = serve_leg(hwc, c2_jobs, c2_results, c2["batched"]["value"], args.serve_requests,
                                    args.serve_load)
         line["served"]["workload"] = "config2"
+        line["table1"] = table1_leg(hwc)
     if args.serve and rank == 0 and world == 1:
         line["served_" + args.config] = serve_leg(hwc, jobs, results, value, args.serve_requests, args.serve_load)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

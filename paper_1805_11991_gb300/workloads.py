@@ -90,8 +90,23 @@ def config2_q31d6():
     return [JobSpec(2, 31, MONIC_NOSUB, 6)]
 
 
+def config4_q27_slice():
+    """2^21 members from the middle of the g=3 q=27 degree-7 job of
+    configuration 4 (2,877 groups of q^2 members): the small case used for
+    detailed profiles of the two-level kernel."""
+    return [JobSpec(3, 27, MONIC_NOSUB, 7, 27 ** 6 // 2, 1 << 21)]
+
+
+def config3_q293_slice():
+    """2^18 of the 2^24 sampled members of the q=293 job of configuration 3:
+    the small case used for profiles of the per-member kernel (17-bit Zech
+    table of F_{293^2} in shared memory)."""
+    return [JobSpec(2, 293, MONIC_NOSUB_SAMPLED, 5, 0, 1 << 18, seed=7, sample_count=1 << 24)]
+
+
 CONFIGS = {"config1": config1, "config2": config2, "config3": config3, "config4": config4,
-           "config5": config5, "config2_q31d5": config2_q31d5, "config2_q31d6": config2_q31d6}
+           "config5": config5, "config2_q31d5": config2_q31d5, "config2_q31d6": config2_q31d6,
+           "config4_q27_slice": config4_q27_slice, "config3_q293_slice": config3_q293_slice}
 
 
 def poisson_arrivals(n: int, rate_per_s: float, seed: int = 11) -> np.ndarray:
