@@ -149,6 +149,22 @@ __device__ __forceinline__ void fan2_zero_digits(const uint32_t *Us, uint32_t j0
     }
 }
 
+// queue the block's flagged points (row top bit: y in F_q, rare for k >= 3):
+// one test of the OR of the 8 rows, the per-point stores only when set
+__device__ __forceinline__ void queue_flagged(const uint32_t (&a)[8], const uint32_t (&ly)[8], uint16_t *rq,
+                                              uint32_t &qn)
+{
+    const uint32_t any = (a[0] | a[1] | a[2] | a[3]) | (a[4] | a[5] | a[6] | a[7]);
+    if ((int)any < 0) {
+#pragma unroll
+        for (int v = 0; v < 8; ++v)
+            if ((int)a[v] < 0) {
+                rq[qn] = (uint16_t)ly[v];
+                qn += 32;
+            }
+    }
+}
+
 // One block of 8 consecutive points x = alpha^(j0 + i) for lane (b, s), with
 // lb = log(b x) of the first point reduced mod L (later points lb + v, not
 // reduced).  Phases over the 8 points so that their lookups overlap: staged
@@ -183,13 +199,9 @@ __device__ __forceinline__ void fan2_block(const Tab T, const uint32_t *__restri
 #pragma unroll
     for (int v = 0; v < 8; ++v) a[v] = rows[ly[v]];
 #pragma unroll
-    for (int v = 0; v < 8; ++v) {
+    for (int v = 0; v < 8; ++v)
         if (GEN && !((okm >> v) & 1u)) a[v] = 0u;
-        if (QUEUE && (int)a[v] < 0) {   // flagged: y in F_q (rare for k >= 3)
-            rq[qn] = (uint16_t)ly[v];
-            qn += 32;
-        }
-    }
+    if (QUEUE) queue_flagged(a, ly, rq, qn);
 }
 
 // One block of 8 orbit points for lane (b, s): the staged log u(x) (U) and
@@ -230,13 +242,9 @@ __device__ __forceinline__ void fan2_block_reps(const Tab T, const uint32_t *__r
 #pragma unroll
     for (int v = 0; v < 8; ++v) a[v] = rows[ly[v]];
 #pragma unroll
-    for (int v = 0; v < 8; ++v) {
+    for (int v = 0; v < 8; ++v)
         if (GEN && !((okm >> v) & 1u)) a[v] = 0u;
-        if (QUEUE && (int)a[v] < 0) {
-            rq[qn] = (uint16_t)ly[v];
-            qn += 32;
-        }
-    }
+    if (QUEUE) queue_flagged(a, ly, rq, qn);
 }
 
 // points of one field for the whole group (all q^2 members), lane role (b, s)
@@ -638,8 +646,14 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
             const uint32_t cc = (uint32_t)lane;
             const uint32_t lc = coefk[cc];
             const int chi_c = (cc == 0) ? 0 : ((lc & 1u) ? -1 : 1);
+            // the members' key slots (global scratch) from the earlier fields,
+            // loaded one member ahead
+            const bool keyed = !J.dense_off && k > 0;
+            unsigned long long knext = keyed ? keys[cc] : 0ull;
             for (uint32_t bb = 0; bb < q; ++bb) {
                 const uint32_t m = bb * q + cc;
+                const unsigned long long kold = knext;
+                if (keyed && bb + 1 < q) knext = keys[m + q];
                 uint32_t tot = 0;
                 for (uint32_t ss = 0; ss < S; ++ss) tot += acc[(ss * q + bb) * q + cc];
                 const int a2 = zs ? (int)(tot & ((1u << zs) - 1u)) : (int)tot;
@@ -650,7 +664,7 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
                 if (orb) {
                     int part = 0;
                     if (J.dense_off) part = k == 1 ? (int)(a1s[m] >> 8) : 0;
-                    else if (k > 0) part = (int16_t)(uint16_t)(keys[m] >> (16 * k));
+                    else if (k > 0) part = (int16_t)(uint16_t)(kold >> (16 * k));
                     Sk = part + (k + 1) * E;
                 }
                 const int N = (int)Q + Sk + inf;
@@ -681,7 +695,7 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
                 } else {
                     // slot k: this member's final a_{k+1}; with orbits, slots of the
                     // multiples (k+1) t collect (k+1) (E or N - Z) as int16
-                    unsigned long long key = k == 0 ? 0ull : keys[m];
+                    unsigned long long key = k == 0 ? 0ull : kold;
                     key = (key & ~(0xFFFFull << (16 * k))) | ((unsigned long long)a16 << (16 * k));
                     if (orb) {
 #pragma unroll
