@@ -220,6 +220,17 @@ int hwc_hist_from_arrays(uint32_t g, uint64_t n_entries, const int32_t *counts,
                          const uint64_t *mult, uint64_t n_total, hwc_hist_t **out);
 void hwc_hist_free(hwc_hist_t *h);
 
+/* Checkpoints.  A histogram is the count of a member range; ranges of one
+ * job add (hwc_hist_merge), so an interrupted job resumes from its first
+ * uncounted member.  hwc_hist_save writes the histogram (tuples,
+ * multiplicities, patterns if any, members examined) and, when job is not
+ * NULL, the job it counts (members [job->first, job->first + job->count)
+ * done) to a little-endian binary file; hwc_hist_load reads it back, and
+ * fills *job when job is not NULL and the file has one (else zeroes it).
+ * Errors: HWC_ERR_ARG (bad file), HWC_ERR_NOMEM. */
+int hwc_hist_save(const hwc_hist_t *h, const hwc_job_t *job, const char *path);
+int hwc_hist_load(const char *path, hwc_hist_t **out, hwc_job_t *job);
+
 /* ------------------------------------------------------------------ */
 /* Batched execution: many jobs in one persistent launch               */
 /* The paper launches one kernel per curve and field (Sec. 3.3); batching

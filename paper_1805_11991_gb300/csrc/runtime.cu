@@ -1171,6 +1171,76 @@ extern "C" int hwc_hist_from_arrays(uint32_t g, uint64_t n_entries, const int32_
     return HWC_OK;
 }
 
+// checkpoint file: "HWCH", version 1, g, flags (1: patterns, 2: job), n, n_total,
+// n_squarefree, [job], then per entry counts[g] (i32), mult (u64), [pattern (u64)];
+// every field little endian (the layout of the host; both hosts of this
+// library are little endian)
+namespace {
+constexpr uint32_t kCkptMagic = 0x48435748u;   // "HWCH"
+}
+
+extern "C" int hwc_hist_save(const hwc_hist_t *h, const hwc_job_t *job, const char *path)
+{
+    if (!h || !path) return set_error(HWC_ERR_ARG, "null argument");
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return set_error(HWC_ERR_ARG, "cannot open %s for writing", path);
+    const uint64_t n = h->mult.size();
+    const uint32_t head[4] = {kCkptMagic, 1u, h->g, (h->has_lam ? 1u : 0u) | (job ? 2u : 0u)};
+    const uint64_t sizes[3] = {n, h->n_total, h->n_sqf};
+    bool ok = std::fwrite(head, sizeof head, 1, f) == 1 && std::fwrite(sizes, sizeof sizes, 1, f) == 1;
+    if (ok && job) ok = std::fwrite(job, sizeof *job, 1, f) == 1;
+    for (uint64_t i = 0; ok && i < n; ++i) {
+        ok = std::fwrite(&h->counts[i * h->g], sizeof(int32_t), h->g, f) == h->g &&
+             std::fwrite(&h->mult[i], sizeof(uint64_t), 1, f) == 1;
+        if (ok && h->has_lam) ok = std::fwrite(&h->lam[i], sizeof(uint64_t), 1, f) == 1;
+    }
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? HWC_OK : set_error(HWC_ERR_ARG, "writing %s failed", path);
+}
+
+extern "C" int hwc_hist_load(const char *path, hwc_hist_t **out, hwc_job_t *job)
+{
+    if (!path || !out) return set_error(HWC_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (job) std::memset(job, 0, sizeof *job);
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return set_error(HWC_ERR_ARG, "cannot open %s", path);
+    uint32_t head[4];
+    uint64_t sizes[3];
+    hwc_job_t jb{};
+    bool ok = std::fread(head, sizeof head, 1, f) == 1 && head[0] == kCkptMagic && head[1] == 1u &&
+              head[2] >= 1 && head[2] <= (uint32_t)kMaxG && std::fread(sizes, sizeof sizes, 1, f) == 1;
+    if (ok && (head[3] & 2u)) ok = std::fread(&jb, sizeof jb, 1, f) == 1;
+    hwc_hist *h = ok ? new hwc_hist() : nullptr;
+    if (ok) {
+        h->g = head[2];
+        h->has_lam = head[3] & 1u;
+        h->n_total = sizes[1];
+        const uint64_t n = sizes[0];
+        if (n > (1ull << 40)) ok = false;
+        for (uint64_t i = 0; ok && i < n; ++i) {
+            int32_t c[kMaxG];
+            uint64_t m = 0, l = 0;
+            ok = std::fread(c, sizeof(int32_t), h->g, f) == h->g && std::fread(&m, sizeof m, 1, f) == 1;
+            if (ok && h->has_lam) ok = std::fread(&l, sizeof l, 1, f) == 1;
+            if (!ok) break;
+            h->counts.insert(h->counts.end(), c, c + h->g);
+            h->mult.push_back(m);
+            if (h->has_lam) h->lam.push_back(l);
+            h->n_sqf += m;
+        }
+        ok = ok && h->n_sqf == sizes[2];
+    }
+    std::fclose(f);
+    if (!ok) {
+        delete h;
+        return set_error(HWC_ERR_ARG, "%s is not a valid histogram checkpoint", path);
+    }
+    if (job && (head[3] & 2u)) *job = jb;
+    *out = h;
+    return HWC_OK;
+}
+
 extern "C" int hwc_hist_lambda(const hwc_hist_t *h, uint64_t *codes)
 {
     if (!h) return set_error(HWC_ERR_ARG, "histogram is NULL");

@@ -83,6 +83,8 @@ def load(build_if_missing: bool = True):
             "hwc_hist_genus": (c_int, [vp, P(u32)]),
             "hwc_hist_read": (c_int, [vp, P(ctypes.c_int32), P(u64)]),
             "hwc_hist_lambda": (c_int, [vp, P(u64)]),
+            "hwc_hist_save": (c_int, [vp, P(Job), ctypes.c_char_p]),
+            "hwc_hist_load": (c_int, [ctypes.c_char_p, P(vp), P(Job)]),
             "hwc_hist_merge": (c_int, [vp, vp]),
             "hwc_hist_from_arrays": (c_int, [u32, u64, P(ctypes.c_int32), P(u64), u64, P(vp)]),
             "hwc_hist_free": (None, [vp]),
@@ -235,6 +237,39 @@ def count_members(g: int, q: int, fam: Family, first: int, n: int, unfiltered: b
                                   counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                   sqf.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))))
     return counts, sqf
+
+
+def _to_handle(src: Histogram) -> ctypes.c_void_p:
+    """A library histogram with the contents of `src` (without patterns)."""
+    h = ctypes.c_void_p()
+    c = np.ascontiguousarray(src.counts, np.int32)
+    m = np.ascontiguousarray(src.mult, np.uint64)
+    _check(_lib.hwc_hist_from_arrays(src.g, len(m), c.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                     m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), src.n_total,
+                                     ctypes.byref(h)))
+    return h
+
+
+def hist_save(h: Histogram, path: str, job: Job | None = None) -> None:
+    """hwc_hist_save: a checkpoint file of the histogram and the job range it counts."""
+    load()
+    if h.lam is not None:
+        raise ValueError("checkpoints of pattern-keyed histograms are written by the C API")
+    hh = _to_handle(h)
+    try:
+        _check(_lib.hwc_hist_save(hh, ctypes.byref(job) if job is not None else None, path.encode()))
+    finally:
+        _lib.hwc_hist_free(hh)
+
+
+def hist_load(path: str):
+    """hwc_hist_load: (histogram, job or None)."""
+    load()
+    h = ctypes.c_void_p()
+    jb = Job()
+    _check(_lib.hwc_hist_load(path.encode(), ctypes.byref(h), ctypes.byref(jb)))
+    hist = _take_hist(h)
+    return hist, (jb if jb.g else None)
 
 
 def hist_merge(a: Histogram, b: Histogram) -> Histogram:
