@@ -266,13 +266,14 @@ def _strip_comments(text: str) -> str:
 
 
 def kernel_source_hash() -> str:
-    """Hash of the CUDA sources with comments and white space removed: a
-    traffic figure stays valid across comment-only edits and lapses on any
-    change of code."""
+    """Hash of the count kernels' device sources (the .cuh headers and the
+    per-degree instantiation files) with comments and white space removed: a
+    traffic figure stays valid across comment-only edits and host-side
+    changes, and lapses on any change of kernel code."""
     h = hashlib.sha256()
     src = os.path.join(ROOT, "paper_1805_11991_gb300", "csrc")
     for f in sorted(os.listdir(src)):
-        if f.endswith((".cu", ".cuh")):
+        if f.endswith(".cuh") or (f.endswith(".cu") and f.startswith(("fan2_", "fanout_", "horner_"))):
             with open(os.path.join(src, f)) as fh:
                 h.update(f.encode() + b"\0" + _strip_comments(fh.read()).encode())
     return h.hexdigest()[:16]
