@@ -28,10 +28,14 @@ namespace {
 
 constexpr int kFan2Warps = 4;                 // smallest block (warps)
 constexpr int kFan2Planes = 10;               // per-lane counts < 1024 between flushes
-constexpr uint32_t kFan2FlushBlocks = 127;    // 8-input blocks per lane between flushes
+// 8-input blocks per lane between flushes: a flush follows as soon as the
+// count reaches 124, and at most 4 blocks are added between the tests, so
+// no position exceeds 127 x 8 = 1016 < 1024
+constexpr uint32_t kFan2FlushBlocks = 124;
 
-// add 8 row words into 10 bit-sliced planes (carry-save tree, ripple of the eights)
-__device__ __forceinline__ void add8_p10(uint32_t (&P)[kFan2Planes], const uint32_t (&a)[8])
+// add 8 row words into the carry-save planes 0..2 (ones, twos, fours); returns
+// the carry of weight 8, to be added into plane 3 and up by the caller
+__device__ __forceinline__ uint32_t csa8(uint32_t (&P)[kFan2Planes], const uint32_t (&a)[8])
 {
     uint32_t tA, tB, fA, fB, e;
     csa(tA, P[0], P[0], a[0], a[1]);
@@ -41,12 +45,25 @@ __device__ __forceinline__ void add8_p10(uint32_t (&P)[kFan2Planes], const uint3
     csa(tB, P[0], P[0], a[6], a[7]);
     csa(fB, P[1], P[1], tA, tB);
     csa(e, P[2], P[2], fA, fB);
+    return e;
+}
+
+// add a carry word of weight 2^B0 into planes B0.. (ripple)
+template <int B0>
+__device__ __forceinline__ void ripple(uint32_t (&P)[kFan2Planes], uint32_t e)
+{
 #pragma unroll
-    for (int b = 3; b < kFan2Planes; ++b) {
+    for (int b = B0; b < kFan2Planes; ++b) {
         const uint32_t c = P[b] & e;
         P[b] ^= e;
         e = c;
     }
+}
+
+// add 8 row words into 10 bit-sliced planes (carry-save tree, ripple of the eights)
+__device__ __forceinline__ void add8_p10(uint32_t (&P)[kFan2Planes], const uint32_t (&a)[8])
+{
+    ripple<3>(P, csa8(P, a));
 }
 
 // add the per-position counts of the planes into the lane's row (2 per row
@@ -321,7 +338,40 @@ __device__ __forceinline__ void group2_field(const KJob &J, int k, const uint8_t
                                                      jq, zw);
             __syncwarp();
         }
-        if (pow2S && nb == 64 && !uzero) {
+        if (pow2S && S <= 2 && nb == 64 && !uzero) {
+            // 32 or 64 points per lane: steps of 4 blocks, whose eights meet in
+            // carry-save planes 3 and 4 before one ripple of weight 32
+            const uint32_t per = 64 / S, i0 = s * per;
+            uint32_t lb = REPS ? 0u : addmod(lam_b, j0 + i0, L);
+            auto blk = [&](uint32_t t0) -> uint32_t {
+                uint32_t a[8];
+                if (REPS) fan2_block_reps<false, QUEUE>(T, rows, Us + i0 + t0, Ds + i0 + t0, L, lam_b, b0, 0u, rq, qn, a);
+                else fan2_block<false, QUEUE>(T, rows, Us + i0 + t0, L, lb, b0, 0u, rq, qn, a);
+                if (!REPS) lb = addmod(lb, 8u % L, L);
+                const uint32_t e = csa8(P, a);
+                if (QUEUE && __any_sync(0xFFFFFFFFu, qn >= 32 * (kFan2Queue - 8 + 1))) {   // more than 8 entries
+                    drain_queue(rq, qn, lane, zdig, zdiv, L, acc_row, zw);
+                    qn = (uint32_t)lane;
+                }
+                return e;
+            };
+            for (uint32_t t0 = 0; t0 < per; t0 += 32) {
+                uint32_t s16a, s16b, s32;
+                const uint32_t e0 = blk(t0);
+                const uint32_t e1 = blk(t0 + 8);
+                csa(s16a, P[3], P[3], e0, e1);
+                const uint32_t e2 = blk(t0 + 16);
+                const uint32_t e3 = blk(t0 + 24);
+                csa(s16b, P[3], P[3], e2, e3);
+                csa(s32, P[4], P[4], s16a, s16b);
+                ripple<5>(P, s32);
+                nblk += 4;
+                if (nblk >= kFan2FlushBlocks) {
+                    flush_planes(P, acc_row, J.q, true);
+                    nblk = 0;
+                }
+            }
+        } else if (pow2S && nb == 64 && !uzero) {
             const uint32_t per = 64 / S, i0 = s * per;
             uint32_t lb = REPS ? 0u : addmod(lam_b, j0 + i0, L);
             for (uint32_t t0 = 0; t0 < per; t0 += 8) {
@@ -330,7 +380,7 @@ __device__ __forceinline__ void group2_field(const KJob &J, int k, const uint8_t
                 else fan2_block<false, QUEUE>(T, rows, Us + i0 + t0, L, lb, b0, 0u, rq, qn, a);
                 if (!REPS) lb = addmod(lb, 8u % L, L);
                 add8_p10(P, a);
-                if (++nblk == kFan2FlushBlocks) {
+                if (++nblk >= kFan2FlushBlocks) {
                     flush_planes(P, acc_row, J.q, true);
                     nblk = 0;
                 }
@@ -352,7 +402,7 @@ __device__ __forceinline__ void group2_field(const KJob &J, int k, const uint8_t
                 else fan2_block<true, QUEUE>(T, rows, Us + i0 + t0, L, lb, b0, okm, rq, qn, a);
                 if (!REPS) lb = addmod(lb, 8u % L, L);
                 add8_p10(P, a);
-                if (++nblk == kFan2FlushBlocks) {
+                if (++nblk >= kFan2FlushBlocks) {
                     flush_planes(P, acc_row, J.q, true);
                     nblk = 0;
                 }
@@ -496,6 +546,118 @@ __device__ __noinline__ uint32_t sqf_mask_for_b(const uint8_t *mulT, const uint8
     return mask;
 }
 
+// sqf_mask_for_b when f' = w has full degree D - 1 (its leading coefficient
+// D c_D is nonzero: p does not divide D): the same steps -- g_b mod w, the
+// matrix of multiplication by g_b on F_q[x]/(w), its upper Hessenberg form,
+// the Hessenberg recurrence for the characteristic polynomial, its values at
+// t = -c -- with every loop bound fixed, so that the matrix and the
+// polynomials stay in registers.  A zero subdiagonal pivot is replaced by the
+// first nonzero entry below it through a row and column swap made of selects.
+template <int D>
+__device__ __noinline__ uint32_t sqf_mask_full(const uint8_t *mulT, const uint8_t *subT, const uint8_t *invT,
+                                               const uint8_t *addT, uint32_t q, uint32_t p, const uint32_t *cg,
+                                               uint32_t b)
+{
+    constexpr int M = D - 1;   // deg w
+    auto mul = [&](uint32_t x, uint32_t y) -> uint32_t { return mulT[x * q + y]; };
+    auto sub = [&](uint32_t x, uint32_t y) -> uint32_t { return subT[x * q + y]; };
+    auto add = [&](uint32_t x, uint32_t y) -> uint32_t { return addT[x * q + y]; };
+    // w = f' / (D c_D), monic
+    uint32_t w[M + 1];
+    w[0] = b;
+#pragma unroll
+    for (int i = 2; i <= D; ++i) w[i - 1] = mul((uint32_t)i % p, cg[i]);
+    const uint32_t wi = invT[w[M]];
+#pragma unroll
+    for (int i = 0; i < M; ++i) w[i] = mul(w[i], wi);
+    // r = g_b mod w, g_b = b x + sum_{i>=2} c_i x^i
+    uint32_t r[D + 1];
+    r[0] = 0;
+    r[1] = b;
+#pragma unroll
+    for (int i = 2; i <= D; ++i) r[i] = cg[i];
+#pragma unroll
+    for (int t = D; t >= M; --t) {
+        const uint32_t cf = r[t];
+        r[t] = 0;
+#pragma unroll
+        for (int i = 0; i < M; ++i) r[t - M + i] = sub(r[t - M + i], mul(cf, w[i]));
+    }
+    // H[i][j]: coefficient i of g_b x^j mod w
+    uint32_t H[M][M];
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+#pragma unroll
+        for (int i = 0; i < M; ++i) H[i][j] = r[i];
+        if (j + 1 < M) {
+            const uint32_t top = r[M - 1];
+#pragma unroll
+            for (int i = M - 1; i >= 1; --i) r[i] = sub(r[i - 1], mul(top, w[i]));
+            r[0] = sub(0, mul(top, w[0]));
+        }
+    }
+    // upper Hessenberg form by similarity
+#pragma unroll
+    for (int j = 0; j + 2 < M; ++j) {
+#pragma unroll
+        for (int i = j + 2; i < M; ++i) {
+            const bool sw = H[j + 1][j] == 0 && H[i][j] != 0;
+#pragma unroll
+            for (int k = 0; k < M; ++k) {
+                const uint32_t x = H[i][k], y = H[j + 1][k];
+                H[i][k] = sw ? y : x;
+                H[j + 1][k] = sw ? x : y;
+            }
+#pragma unroll
+            for (int k = 0; k < M; ++k) {
+                const uint32_t x = H[k][i], y = H[k][j + 1];
+                H[k][i] = sw ? y : x;
+                H[k][j + 1] = sw ? x : y;
+            }
+        }
+        // a zero pivot leaves a zero column below it: every f is 0
+        const uint32_t iv = invT[H[j + 1][j]];
+#pragma unroll
+        for (int i = j + 2; i < M; ++i) {
+            const uint32_t f = mul(H[i][j], iv);
+#pragma unroll
+            for (int k = 0; k < M; ++k) H[i][k] = sub(H[i][k], mul(f, H[j + 1][k]));
+#pragma unroll
+            for (int k = 0; k < M; ++k) H[k][j + 1] = add(H[k][j + 1], mul(f, H[k][i]));
+        }
+    }
+    // p_k(t) = (t - h_kk) p_{k-1} - sum_{i<k} h_ik (prod_{j=i+1..k} h_{j,j-1}) p_{i-1}  (1-based)
+    uint32_t P[M + 1][M + 1];
+    P[0][0] = 1;
+#pragma unroll
+    for (int k = 1; k <= M; ++k) {
+#pragma unroll
+        for (int e = 0; e <= k; ++e) {
+            uint32_t v = (e >= 1) ? P[k - 1][e - 1] : 0u;
+            if (e <= k - 1) v = sub(v, mul(H[k - 1][k - 1], P[k - 1][e]));
+            P[k][e] = v;
+        }
+        uint32_t prod = 1;
+#pragma unroll
+        for (int i = k - 1; i >= 1; --i) {
+            prod = mul(prod, H[i][i - 1]);
+            const uint32_t f = mul(H[i - 1][k - 1], prod);
+#pragma unroll
+            for (int e = 0; e <= i - 1; ++e) P[k][e] = sub(P[k][e], mul(f, P[i - 1][e]));
+        }
+    }
+    // member c square-free iff chi(-c) != 0
+    uint32_t mask = 0;
+    for (uint32_t c = 0; c < q; ++c) {
+        const uint8_t *mrow = mulT + subT[c] * q;   // times t = -c
+        uint32_t v = 1;
+#pragma unroll
+        for (int e = M - 1; e >= 0; --e) v = addT[mrow[v] * q + P[M][e]];
+        if (v) mask |= 1u << c;
+    }
+    return mask;
+}
+
 // one group of q^2 members (c_1, c_0 free) for one warp
 template <int D>
 __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, const uint8_t *smem,
@@ -548,7 +710,13 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
     }
     __syncwarp();
     if ((uint32_t)lane < q) {
-        const uint32_t mask = sqf_mask_for_b<D>(mulT, subT, invT, addT, q, J.p, gc, (uint32_t)lane);
+        uint32_t mask;
+        if constexpr (D <= 8) {   // f' of full degree: the fixed-shape form
+            if (mulT[(D % J.p) * q + gc[D]] != 0) mask = sqf_mask_full<D>(mulT, subT, invT, addT, q, J.p, gc, (uint32_t)lane);
+            else mask = sqf_mask_for_b<D>(mulT, subT, invT, addT, q, J.p, gc, (uint32_t)lane);
+        } else {
+            mask = sqf_mask_for_b<D>(mulT, subT, invT, addT, q, J.p, gc, (uint32_t)lane);
+        }
         // bits b*q .. b*q + q-1 of the member mask
         const uint32_t bit0 = (uint32_t)lane * q;
         const uint32_t w0 = bit0 >> 5, sh = bit0 & 31u;
