@@ -42,7 +42,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_1805_11991_gb300.workloads import CONFIGS, JobSpec  # noqa: E402
+from paper_1805_11991_gb300.workloads import CONFIGS, MONIC_NOSUB_SAMPLED, JobSpec  # noqa: E402
 
 METRIC = "point evals/s (square-free members x sum_k q^k), batched persistent launch"
 UNIT = "evals/s"
@@ -120,11 +120,14 @@ def table_reads(spec: JobSpec, n_squarefree: int, method: int) -> float:
         chain over c_1..c_d plus one fan-out row;
       2, fan-out over (c_1, c_0) (groups of q^2 members): per group and
         point, the chain over c_2..c_d, one Zech addition per c_1 != 0 and
-        one fan-out row per c_1: chain + 2q - 1."""
+        one fan-out row per c_1: chain + 2q - 1.  A sampled family on this
+        kernel is counted over every group of its family (the samples'
+        multiplicities as weights)."""
     d, q = spec.degree, spec.q
     pts = points_per_member(spec)
     if method == 2:
-        return spec.n() / q ** 2 * pts * (chain_reads(spec, 2) + 2 * q - 1)
+        members = q ** (d - 1) if spec.kind == MONIC_NOSUB_SAMPLED else spec.n()
+        return members / q ** 2 * pts * (chain_reads(spec, 2) + 2 * q - 1)
     if method == 1:
         return spec.n() / q * pts * (chain_reads(spec, 1) + 1)
     return n_squarefree * pts * (d - 1) * (q - 1) / q

@@ -149,8 +149,12 @@ int hwc_family_size(uint32_t q, const hwc_family_t *fam, uint64_t *n);
 #define HWC_FLAG_HORNER 0x4u      /* force the per-member Horner kernel        */
 /* Kernels: enumerated families with q <= 31 use the two-level fan-out (q^2
  * members sharing c_2..c_d per warp), q <= 63 the one-level c_0 fan-out (q
- * members per warp), everything else (sampled families, larger q) the
- * per-member Horner kernel.  All give identical counts. */
+ * members per warp), everything else (larger q, reduced families, sparse
+ * samples) the per-member Horner kernel.  A sampled family with q <= 31 and
+ * at least one sample per 32 members of HWC_FAM_MONIC_NOSUB (fewer than 2^27
+ * samples) runs the two-level fan-out over the whole family, each member
+ * weighted by how often the samples drew it (4 bytes of device memory per
+ * member, cleared and filled in every run).  All give identical counts. */
 #define HWC_FLAG_NO_TUNE 0x8u     /* skip the autotuner, use defaults          */
 #define HWC_FLAG_TIMING 0x10u     /* time the count kernel(s) with CUDA events */
 #define HWC_FLAG_FAN1 0x20u       /* one-level c_0 fan-out even where the

@@ -730,15 +730,20 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
     for (uint32_t t = 0; t < nw; ++t) {
         const uint32_t m = t * 32 + lane;
         const uint64_t idx = base + m;
-        const bool v = m < qq && idx >= J.first && idx < J.first + J.count;
+        bool v = m < qq && idx >= J.first && idx < J.first + J.count;
+        // sampled family: the member's multiplicity among the samples (0: not drawn)
+        const uint32_t w = (J.mweight && v) ? J.mweight[idx] : 1u;
+        v = v && w != 0;
         const bool sq = v && ((sqfw[t] >> lane) & 1u);
         const unsigned vm = __ballot_sync(0xFFFFFFFFu, v);
         const unsigned sm = __ballot_sync(0xFFFFFFFFu, sq);
+        const uint32_t wv = J.mweight ? __reduce_add_sync(0xFFFFFFFFu, v ? w : 0u) : (uint32_t)__popc(vm);
+        const uint32_t ws = J.mweight ? __reduce_add_sync(0xFFFFFFFFu, sq ? w : 0u) : (uint32_t)__popc(sm);
         __syncwarp();
         if (lane == 0) {
-            sqfw[t] = sm;   // square-free and in range
-            st.examined += __popc(vm);
-            st.sqf += __popc(sm);
+            sqfw[t] = sm;   // square-free, in range (and drawn)
+            st.examined += wv;
+            st.sqf += ws;
         }
         anyv |= vm;
         anys |= sm;
@@ -855,10 +860,11 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
                         const uint32_t k1 = G == 2 ? ((a1s[m] & 0xFFu) + 32768u - 128u) : a16;
                         const int i1 = (int)k1 - 32768 + J.dense_b1;
                         const int i2 = G == 2 ? a + J.dense_b2 : 0;
+                        const uint32_t w = J.mweight ? J.mweight[base + m] : 1u;
                         if (i1 >= 0 && i1 <= 2 * J.dense_b1 && i2 >= 0 && i2 <= 2 * J.dense_b2)
-                            atomicAdd(&dense[(uint32_t)i1 * J.dense_w2 + (uint32_t)i2], 1u);
+                            atomicAdd(&dense[(uint32_t)i1 * J.dense_w2 + (uint32_t)i2], w);
                         else   // outside the Hasse-Weil box: not for a smooth curve
-                            hist_insert(J, G == 2 ? ((unsigned long long)a16 << 16 | k1) : a16, 1u);
+                            hist_insert(J, G == 2 ? ((unsigned long long)a16 << 16 | k1) : a16, w);
                     }
                 } else {
                     // slot k: this member's final a_{k+1}; with orbits, slots of the
@@ -891,7 +897,9 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
         if (sq) {
             const unsigned long long key = keys[m];
             const unsigned peers = __match_any_sync(smask, key);
-            if (lane == __ffs(peers) - 1) hist_insert(J, key, __popc(peers));
+            // equal keys counted once: the peers' members, or their multiplicities
+            const uint32_t cnt = J.mweight ? __reduce_add_sync(peers, J.mweight[base + m]) : (uint32_t)__popc(peers);
+            if (lane == __ffs(peers) - 1) hist_insert(J, key, cnt);
         }
     }
     __syncwarp();

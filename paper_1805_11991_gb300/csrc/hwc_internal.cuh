@@ -168,6 +168,13 @@ struct KJob {
     uint32_t fq_off;                  // byte offset of mul | sub | inv | add in smem
     const uint32_t *coord2;           // method 2, g = 2: coordinates of F_{q^2} (Tables::d_coord2)
     uint32_t coord_off, pad4;         // byte offset of coord2 in smem; 0: not staged
+    // sampled family counted by the two-level kernel over the whole family:
+    // mweight[i] = how often member i of HWC_FAM_MONIC_NOSUB was drawn by the
+    // samples [s_first, s_first + s_count) (launch_sample_weights); the kernel
+    // counts member i with that weight (0: not drawn).  first / count then
+    // cover the whole family.  Null: every member in range has weight 1.
+    uint32_t *mweight;
+    uint64_t s_first, s_count;
     // outputs
     unsigned long long *hkeys;        // [hmask+1]
     unsigned long long *hcounts;      // [hmask+1]
@@ -194,6 +201,9 @@ int launch_persistent(int D, uint32_t method, uint32_t words, const KJob *d_jobs
                       unsigned long long *d_counter, uint32_t max_smem, const LaunchShape &sh,
                       cudaStream_t s);
 int launch_compact(const KJob *d_jobs, uint32_t n_jobs, cudaStream_t s);
+// the multiplicities kj.mweight of a sampled job counted by the two-level
+// kernel: cleared, then one atomic add per sample (stream-ordered)
+int launch_sample_weights(const KJob &kj, cudaStream_t s);
 // raise the dynamic shared memory limit of the count kernels (once per device)
 int prepare_count_kernels(void);
 int max_ctas_per_sm(int D, uint32_t method, uint32_t words, int block, uint32_t smem_bytes,
@@ -210,6 +220,12 @@ struct TuneChoice {
     bool no_triple = false;   // shared Zech tables in the doubled layout only
 };
 bool layout_job_smem(KJob &j, uint32_t smem_limit, bool no_triple = false);
+// a sampled job counted by the two-level kernel over its whole family, with
+// the samples' multiplicities as weights (KJob::mweight)
+inline bool needs_weights(const KJob &kj) { return kj.kind == HWC_FAM_MONIC_NOSUB_SAMPLED && kj.method == 2; }
+// fill_kjob flag (internal): keep sampled families on the per-member kernel
+// (per-sample outputs need the members in sample order)
+constexpr uint32_t kFlagNoWeights = 1u << 31;
 // the points field k (1-based) evaluates: one per Frobenius orbit (orbits,
 // k >= 2) or all of F_Q^x; and the two-level kernel's zero shift
 void set_points(KJob &kj, uint32_t k, const Tables *t, bool orbits);

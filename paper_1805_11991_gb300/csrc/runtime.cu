@@ -403,6 +403,34 @@ int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n, uint32_t flags, co
         kj.zdiv[k - 1] = sdiv == 1 ? 0u : (uint32_t)(((1ull << 32) + sdiv - 1) / sdiv);
     }
     const uint32_t limit = device_smem_optin() - 4096;   // static smem of the kernels
+    // a sampled family with q <= 31 drawn densely (at least one sample per 32
+    // members): the two-level kernel counts every member of the family once,
+    // with its multiplicity among the samples as weight (the weights take 4
+    // bytes per member, at most 16 GB; fewer than 2^27 samples keep the sums
+    // of 32 weights below 2^32)
+    const bool weighted = jb.family.kind == HWC_FAM_MONIC_NOSUB_SAMPLED && jb.q <= 31 &&
+                          !(flags & (HWC_FLAG_HORNER | HWC_FLAG_FAN1 | HWC_FLAG_LAMBDA | kFlagNoWeights)) &&
+                          !(tc && tc->method >= 0 && tc->method != 2) && jb.count >= kj.fam_mz / 32 &&
+                          jb.count < (1ull << 27) && kj.fam_mz <= (1ull << 32);
+    if (weighted) {
+        const uint64_t qq = (uint64_t)jb.q * jb.q;
+        kj.method = 2;
+        kj.words = 1;
+        kj.s_first = jb.first;
+        kj.s_count = jb.count;
+        kj.first = 0;
+        kj.count = kj.fam_mz;
+        kj.first_group = 0;
+        kj.n_tiles = kj.fam_mz / qq;
+        if (layout_job_smem(kj, limit, no_triple)) return HWC_OK;
+        kj.first = jb.first;   // tables do not fit: per-member Horner over the samples
+        kj.count = jb.count;
+        kj.s_first = kj.s_count = 0;
+        kj.first_group = 0;
+        kj.method = 0;
+        kj.words = 0;
+        kj.n_tiles = (jb.count + kTileMembers - 1) / kTileMembers;
+    }
     if (fan && jb.q <= 31 && !(flags & HWC_FLAG_FAN1) && !(tc && tc->method == 1)) {
         // two-level fan-out: groups of q^2 members
         kj.method = 2;
@@ -566,6 +594,7 @@ struct hwc_batch {
     uint64_t d2h_last = 0;
     int device = 0;
     uint32_t launches_per_run = 0;
+    uint32_t weight_launches = 0;    // sampled jobs whose multiplicities are scattered each run
     // persistent batches with several launch groups: the groups after the
     // first run on side streams (forked from and joined to the launch
     // stream), so the tail of one launch overlaps the others
@@ -614,6 +643,8 @@ static int batch_enqueue(hwc_batch *b, cudaStream_t s, bool capturing)
                                  cudaMemcpyHostToDevice, s));
     int rc = launch_clear(b->d_jobs, nj, b->d_counters, (uint32_t)b->groups.size(), s);
     if (rc) return rc;
+    for (const HostJob &hj : b->jobs)   // multiplicities of the samples counted over whole families
+        if ((rc = launch_sample_weights(hj.kj, s))) return rc;
     // inside a graph capture an event record must be an external node to time anything
     if (b->t0) HWC_CUDA_TRY(capturing ? cudaEventRecordWithFlags(b->t0, s, cudaEventRecordExternal)
                                       : cudaEventRecord(b->t0, s));
@@ -770,10 +801,12 @@ static int batch_create_impl(const hwc_job_t *jobs, size_t n, uint32_t flags, ui
         kj.hmask = cap - 1;
         if ((rc = dalloc(b, &kj.hkeys, cap)) || (rc = dalloc(b, &kj.hcounts, cap)) ||
             (rc = dalloc(b, &kj.stats, 4)) || (rc = dalloc(b, &kj.out_keys, cap)) ||
-            (rc = dalloc(b, &kj.out_counts, cap)) || (rc = dalloc(b, &kj.n_out, 1))) {
+            (rc = dalloc(b, &kj.out_counts, cap)) || (rc = dalloc(b, &kj.n_out, 1)) ||
+            (needs_weights(kj) && (rc = dalloc(b, &kj.mweight, kj.fam_mz)))) {
             batch_release(b);
             return rc;
         }
+        if (needs_weights(kj)) ++b->weight_launches;
         // plain runs: every job is a group of its own (one launch per job)
         if (b->groups.empty() || (flags & HWC_FLAG_PLAIN) || b->groups.back().D != (int)kj.d ||
             b->groups.back().method != kj.method || b->groups.back().words != kj.words ||
@@ -854,7 +887,7 @@ static int batch_create_impl(const hwc_job_t *jobs, size_t n, uint32_t flags, ui
             return set_error(HWC_ERR_CUDA, "cudaEventCreate failed");
         }
     }
-    b->launches_per_run = 2 + (uint32_t)b->groups.size();
+    b->launches_per_run = 2 + (uint32_t)b->groups.size() + b->weight_launches;
     if (!(flags & HWC_FLAG_PLAIN) && b->groups.size() > 1) {   // plain runs stay one launch after another
         bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
         for (size_t g = 1; ok && g < b->groups.size(); ++g) {
@@ -1062,7 +1095,7 @@ extern "C" int hwc_count_members(uint32_t g, uint32_t q, const hwc_family_t *fam
     rc = prepare_count_kernels();
     if (rc) return rc;
     KJob kj;
-    rc = fill_kjob(j, kj, &fam_n, flags & (HWC_FLAG_HORNER | HWC_FLAG_FAN1 | HWC_FLAG_ALL_POINTS));
+    rc = fill_kjob(j, kj, &fam_n, (flags & (HWC_FLAG_HORNER | HWC_FLAG_FAN1 | HWC_FLAG_ALL_POINTS)) | kFlagNoWeights);
     if (rc) return rc;
     if (count == 0) return HWC_OK;
     kj.unfiltered = unfiltered ? 1u : 0u;

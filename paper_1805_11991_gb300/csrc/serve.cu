@@ -155,10 +155,12 @@ int admit(hwc_server *s, Request *r)
 {
     KJob &kj = r->kj;
     const uint64_t cap = kj.hmask + 1ull;
-    const uint64_t bytes[7] = {8 * cap, 8 * cap, 8 * 4, 8 * cap, 8 * cap, 8, sizeof(KJob)};
-    void *ptrs[7];
-    int rc = ralloc_all(s, r, bytes, ptrs, 7);
+    const uint64_t bytes[8] = {8 * cap, 8 * cap, 8 * 4, 8 * cap, 8 * cap, 8, sizeof(KJob),
+                               needs_weights(kj) ? 4 * kj.fam_mz : 0};
+    void *ptrs[8];
+    int rc = ralloc_all(s, r, bytes, ptrs, 8);
     if (rc) return rc;
+    if (needs_weights(kj)) kj.mweight = (uint32_t *)ptrs[7];
     kj.hkeys = (unsigned long long *)ptrs[0];
     kj.hcounts = (unsigned long long *)ptrs[1];
     kj.stats = (unsigned long long *)ptrs[2];
@@ -169,6 +171,7 @@ int admit(hwc_server *s, Request *r)
     HWC_CUDA_TRY(cudaMemcpyAsync(r->d_one, &kj, sizeof kj, cudaMemcpyHostToDevice, s->aux));
     rc = launch_clear(r->d_one, 1, nullptr, 0, s->aux);
     if (rc) return rc;
+    if ((rc = launch_sample_weights(kj, s->aux))) return rc;   // the samples' multiplicities
     HWC_CUDA_TRY(cudaEventRecord(s->ev_admit, s->aux));
     HWC_CUDA_TRY(cudaStreamWaitEvent(s->stream, s->ev_admit, 0));
     return HWC_OK;
@@ -467,7 +470,7 @@ extern "C" int hwc_serve_submit(hwc_server_t *s, const hwc_job_t *job, uint64_t 
         return rc;
     }
     r->kj.hmask = hash_capacity(r->kj.g, r->kj.q, job->count, 1) - 1;
-    r->bytes = 32ull * (r->kj.hmask + 1ull) + 4096;
+    r->bytes = 32ull * (r->kj.hmask + 1ull) + 4096 + (needs_weights(r->kj) ? 4 * r->kj.fam_mz : 0);
     {
         std::lock_guard<std::mutex> lk(s->mu);
         for (uint32_t k = 1; k <= job->g; ++k)
