@@ -343,7 +343,8 @@ int hwc_curve_count(uint32_t q, uint32_t k, uint32_t d, uint64_t n, const uint32
  *    HWC_NOALLOC_SCRATCH_BYTES (32768 hash slots, about 512 KiB), which every
  *    GPU that loads the library holds until the process exits.
  *  - The job must fit that array: jobs whose histogram could need more than
- *    32768 hash slots (min(count, Hasse-Weil box) above 16384) are rejected
+ *    32768 hash slots (min(count, Hasse-Weil box, number of real Weil
+ *    polynomials of degree g for q) above 16384) are rejected
  *    with HWC_ERR_TOO_LARGE before anything runs.
  *  - tables[k-1] (k = 1..g) are handles from hwc_field_tables(q, k), built
  *    beforehand; they are read, not changed.

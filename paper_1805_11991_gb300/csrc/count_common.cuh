@@ -318,7 +318,7 @@ __device__ __forceinline__ void hist_insert(const KJob &J, unsigned long long ke
 }
 
 struct WarpStats {
-    unsigned long long examined = 0;   // members in range (weighted by their draws for sampled families)
+    uint32_t examined = 0;   // members in range (weighted by their draws for sampled families, < 2^27)
     unsigned long long sqf = 0;   // square-free members (weighted for reduced families)
 };
 

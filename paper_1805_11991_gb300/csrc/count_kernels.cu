@@ -106,8 +106,9 @@ KernelFn fan_kernel(int D, int W, bool persistent)
     }
 }
 
-KernelFn fan2_kernel(int D)
+KernelFn fan2_kernel(int D, bool weighted)
 {
+    if (weighted) return D <= 6 ? fan2_kernel_wa(D) : fan2_kernel_wb(D);
     return D <= 6 ? fan2_kernel_a(D) : fan2_kernel_b(D);
 }
 
@@ -127,7 +128,7 @@ int prepare_count_kernels(void)
     const int optin = (int)device_smem_optin();
     for (int D = 3; D <= kMaxD; ++D) {
         for (KernelFn fn : {persistent_fn(D), persistent_fn(D, 768), fan_kernel(D, 1, true), fan_kernel(D, 2, true),
-                            fan2_kernel(D)}) {
+                            fan2_kernel(D, false), fan2_kernel(D, true)}) {
             if (!fn) continue;   // no kernel for this degree and row width
             cudaFuncAttributes fa{};
             HWC_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));   // static smem counts against the limit
@@ -159,7 +160,7 @@ uint32_t device_smem_optin(void)
 // up to 768 (chosen by the block size)
 static KernelFn kernel_for(int D, uint32_t method, uint32_t words, bool persistent, int block)
 {
-    if (method == 2) return fan2_kernel(D);
+    if (method == 2) return fan2_kernel(D, words == 2);   // words 2: the weighted (sampled) variant
     if (method == 1) return fan_kernel(D, (int)words, persistent);
     (void)persistent;   // every run is a persistent launch (a plain run has one job per launch)
     return persistent_fn(D, block);

@@ -658,8 +658,11 @@ __device__ __noinline__ uint32_t sqf_mask_full(const uint8_t *mulT, const uint8_
     return mask;
 }
 
-// one group of q^2 members (c_1, c_0 free) for one warp
-template <int D>
+// one group of q^2 members (c_1, c_0 free) for one warp.  W: a sampled
+// family counted over its whole family, each member with its multiplicity
+// among the samples (KJob::mweight; a separate instantiation, so that the
+// unweighted code stays as it is)
+template <int D, bool W>
 __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, const uint8_t *smem,
                                                uint8_t *wsm, int lane, WarpStats &st)
 {
@@ -727,26 +730,44 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
     }
     __syncwarp();
     uint32_t anyv = 0, anys = 0;
-    for (uint32_t t = 0; t < nw; ++t) {
-        const uint32_t m = t * 32 + lane;
-        const uint64_t idx = base + m;
-        bool v = m < qq && idx >= J.first && idx < J.first + J.count;
-        // sampled family: the member's multiplicity among the samples (0: not drawn)
-        const uint32_t w = (J.mweight && v) ? J.mweight[idx] : 1u;
-        v = v && w != 0;
-        const bool sq = v && ((sqfw[t] >> lane) & 1u);
-        const unsigned vm = __ballot_sync(0xFFFFFFFFu, v);
-        const unsigned sm = __ballot_sync(0xFFFFFFFFu, sq);
-        const uint32_t wv = J.mweight ? __reduce_add_sync(0xFFFFFFFFu, v ? w : 0u) : (uint32_t)__popc(vm);
-        const uint32_t ws = J.mweight ? __reduce_add_sync(0xFFFFFFFFu, sq ? w : 0u) : (uint32_t)__popc(sm);
-        __syncwarp();
-        if (lane == 0) {
-            sqfw[t] = sm;   // square-free, in range (and drawn)
-            st.examined += wv;
-            st.sqf += ws;
+    if constexpr (W) {
+        for (uint32_t t = 0; t < nw; ++t) {
+            const uint32_t m = t * 32 + lane;
+            const uint64_t idx = base + m;
+            bool v = m < qq && idx >= J.first && idx < J.first + J.count;
+            const uint32_t w = v ? J.mweight[idx] : 0u;   // multiplicity among the samples (0: not drawn)
+            v = v && w != 0;
+            const bool sq = v && ((sqfw[t] >> lane) & 1u);
+            const unsigned vm = __ballot_sync(0xFFFFFFFFu, v);
+            const unsigned sm = __ballot_sync(0xFFFFFFFFu, sq);
+            const uint32_t wv = __reduce_add_sync(0xFFFFFFFFu, v ? w : 0u);
+            const uint32_t ws = __reduce_add_sync(0xFFFFFFFFu, sq ? w : 0u);
+            __syncwarp();
+            if (lane == 0) {
+                sqfw[t] = sm;   // square-free, in range and drawn
+                st.examined += wv;
+                st.sqf += ws;
+            }
+            anyv |= vm;
+            anys |= sm;
         }
-        anyv |= vm;
-        anys |= sm;
+    } else {
+        for (uint32_t t = 0; t < nw; ++t) {
+            const uint32_t m = t * 32 + lane;
+            const uint64_t idx = base + m;
+            const bool v = m < qq && idx >= J.first && idx < J.first + J.count;
+            const bool sq = v && ((sqfw[t] >> lane) & 1u);
+            const unsigned vm = __ballot_sync(0xFFFFFFFFu, v);
+            const unsigned sm = __ballot_sync(0xFFFFFFFFu, sq);
+            __syncwarp();
+            if (lane == 0) {
+                sqfw[t] = sm;   // square-free and in range
+                st.examined += __popc(vm);
+                st.sqf += __popc(sm);
+            }
+            anyv |= vm;
+            anys |= sm;
+        }
     }
     __syncwarp();
     if ((J.unfiltered ? anyv : anys) == 0) {
@@ -860,7 +881,8 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
                         const uint32_t k1 = G == 2 ? ((a1s[m] & 0xFFu) + 32768u - 128u) : a16;
                         const int i1 = (int)k1 - 32768 + J.dense_b1;
                         const int i2 = G == 2 ? a + J.dense_b2 : 0;
-                        const uint32_t w = J.mweight ? J.mweight[base + m] : 1u;
+                        uint32_t w = 1;
+                        if constexpr (W) w = J.mweight[base + m];
                         if (i1 >= 0 && i1 <= 2 * J.dense_b1 && i2 >= 0 && i2 <= 2 * J.dense_b2)
                             atomicAdd(&dense[(uint32_t)i1 * J.dense_w2 + (uint32_t)i2], w);
                         else   // outside the Hasse-Weil box: not for a smooth curve
@@ -898,7 +920,9 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
             const unsigned long long key = keys[m];
             const unsigned peers = __match_any_sync(smask, key);
             // equal keys counted once: the peers' members, or their multiplicities
-            const uint32_t cnt = J.mweight ? __reduce_add_sync(peers, J.mweight[base + m]) : (uint32_t)__popc(peers);
+            uint32_t cnt;
+            if constexpr (W) cnt = __reduce_add_sync(peers, J.mweight[base + m]);
+            else cnt = __popc(peers);
             if (lane == __ffs(peers) - 1) hist_insert(J, key, cnt);
         }
     }
@@ -923,7 +947,7 @@ __device__ void flush_dense(const KJob &J, const uint8_t *smem)
 
 // threads per CTA at most: 24 warps at <= 80 registers for degrees <= 6, 16
 // warps above (whose longer coefficient arrays would spill at 80)
-template <int D>
+template <int D, bool W>
 __global__ void __launch_bounds__(D <= 6 ? 768 : 512, 1)
     k_fan2_persistent(const KJob *__restrict__ jobs, const uint64_t *__restrict__ item_start, uint32_t n_jobs,
                       uint64_t n_items, unsigned long long *counter, uint32_t item_tiles)
@@ -960,7 +984,7 @@ __global__ void __launch_bounds__(D <= 6 ? 768 : 512, 1)
         uint8_t *wsm = smem + J.warp_off + warp * J.warp_bytes;
         const uint64_t t0 = (item - item_start[jb]) * item_tiles;
         const uint64_t t1 = min(t0 + item_tiles, J.n_tiles);
-        for (uint64_t t = t0 + warp; t < t1; t += nwp) process_group2<D>(J, t, smem, wsm, lane, st);
+        for (uint64_t t = t0 + warp; t < t1; t += nwp) process_group2<D, W>(J, t, smem, wsm, lane, st);
         __syncthreads();
     }
     if (cur >= 0) {
@@ -969,10 +993,10 @@ __global__ void __launch_bounds__(D <= 6 ? 768 : 512, 1)
     }
 }
 
-template <int D>
+template <int D, bool W = false>
 const void *fan2_pick()
 {
-    return (const void *)k_fan2_persistent<D>;
+    return (const void *)k_fan2_persistent<D, W>;
 }
 
 }  // namespace

@@ -151,7 +151,8 @@ struct KJob {
     // c_0 fan-out (method 1): groups of q members that differ only in c_0
     uint32_t method;                  // 0 Horner tiles of 32 members, 1 fan-out groups of q,
                                       // 2 two-level fan-out groups of q^2
-    uint32_t words;                   // row words: 1 (q <= 31) or 2 (q <= 63)
+    uint32_t words;                   // method 1: row words, 1 (q <= 31) or 2 (q <= 63);
+                                      // method 2: 1, or 2 for the weighted variant (mweight)
     uint64_t first_group;             // group of member `first`
     const void *rows[kMaxG];          // d_rows32 / d_rows64
     const uint8_t *zdig[kMaxG];
@@ -168,13 +169,6 @@ struct KJob {
     uint32_t fq_off;                  // byte offset of mul | sub | inv | add in smem
     const uint32_t *coord2;           // method 2, g = 2: coordinates of F_{q^2} (Tables::d_coord2)
     uint32_t coord_off, pad4;         // byte offset of coord2 in smem; 0: not staged
-    // sampled family counted by the two-level kernel over the whole family:
-    // mweight[i] = how often member i of HWC_FAM_MONIC_NOSUB was drawn by the
-    // samples [s_first, s_first + s_count) (launch_sample_weights); the kernel
-    // counts member i with that weight (0: not drawn).  first / count then
-    // cover the whole family.  Null: every member in range has weight 1.
-    uint32_t *mweight;
-    uint64_t s_first, s_count;
     // outputs
     unsigned long long *hkeys;        // [hmask+1]
     unsigned long long *hcounts;      // [hmask+1]
@@ -185,6 +179,13 @@ struct KJob {
     unsigned long long *out_keys;     // compacted histogram [hmask+1]
     unsigned long long *out_counts;
     unsigned long long *n_out;        // number of compacted entries
+    // sampled family counted by the two-level kernel over the whole family:
+    // mweight[i] = how often member i of HWC_FAM_MONIC_NOSUB was drawn by the
+    // samples [s_first, s_first + s_count) (launch_sample_weights); the kernel
+    // counts member i with that weight (0: not drawn).  first / count then
+    // cover the whole family.  Null: every member in range has weight 1.
+    uint32_t *mweight;
+    uint64_t s_first, s_count;
 };
 
 // launch helpers (count_kernels.cu)
@@ -254,9 +255,11 @@ const void *fan_kernel_c(int D, int W, bool persistent);   // fanout_c.cu, D = 6
 const void *fan_kernel_d(int D, int W, bool persistent);   // fanout_d.cu, D = 7
 const void *fan_kernel_f(int D, int W, bool persistent);   // fanout_f.cu, D = 8
 // two-level fan-out kernels (fanout2.cuh), q <= 31
-const void *fan2_kernel(int D);
+const void *fan2_kernel(int D, bool weighted);
 const void *fan2_kernel_a(int D);   // fan2_a.cu, D = 3..6
 const void *fan2_kernel_b(int D);   // fan2_b.cu, D = 7..10
+const void *fan2_kernel_wa(int D);  // fan2_wa.cu, D = 3..6, members weighted by their draws
+const void *fan2_kernel_wb(int D);  // fan2_wb.cu, D = 7..10
 constexpr int kFan2WarpsHost = 4;   // warps per CTA of the two-level kernel
 // Per-warp shared scratch of the two-level kernel for q (S = floor(32/q)
 // lanes per value of c_1; offsets in bytes):

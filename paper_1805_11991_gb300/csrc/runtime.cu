@@ -265,6 +265,53 @@ static uint64_t hasse_weil_box(uint32_t g, uint32_t q)
     return box > 1e18 ? (uint64_t)1e18 : (uint64_t)box;
 }
 
+// Upper bound on the number of distinct keys (a_1..a_g) of square-free
+// members for g <= 3: the L-polynomial of a curve of genus g determines them
+// (Newton's identities) and has all roots of absolute value sqrt(q), so its
+// real Weil polynomial h(x) = prod (x - r_i) is monic with integer
+// coefficients (c_1, ..., c_g), an integer shift of the L-polynomial's, and
+// all roots r_i real in [-m, m], m = 2 sqrt(q).  Counted by the admissible
+// range of c_g for each (c_1, .., c_{g-1}), each range widened by one integer on
+// both sides against rounding.  0 for g > 3 (not counted).
+static uint64_t weil_poly_bound(uint32_t g, uint32_t q)
+{
+    const double m = 2.0 * std::sqrt((double)q);
+    auto range = [](double lo, double hi) -> uint64_t {   // integers in [lo - 1, hi + 1]
+        const double a = std::ceil(lo - 1.0), b = std::floor(hi + 1.0);
+        return b >= a ? (uint64_t)(b - a) + 1 : 0;
+    };
+    if (g == 1) return 2 * (uint64_t)std::floor(m) + 3;
+    const int64_t c1max = (int64_t)std::floor((double)g * m) + 1;
+    uint64_t n = 0;
+    if (g == 2) {
+        // x^2 + c1 x + c2: real roots (c2 <= c1^2 / 4) in [-m, m] (h(+-m) >= 0)
+        for (int64_t c1 = -c1max; c1 <= c1max; ++c1) {
+            const double a = (double)c1;
+            if (std::fabs(a) > 2 * m + 1) continue;
+            n += range(m * std::fabs(a) - m * m, a * a / 4);
+        }
+        return n;
+    }
+    if (g == 3) {
+        // x^3 + c1 x^2 + c2 x + c3 = f(x) + c3: both critical points in
+        // [-m, m] and f(x_max) + c3 >= 0 >= f(x_min) + c3, f(-m) + c3 <= 0 <= f(m) + c3
+        const int64_t c2lo = -(int64_t)std::ceil(3 * m * m) - 1, c2hi = (int64_t)std::ceil(3 * m * m) + 1;
+        for (int64_t c1 = -c1max; c1 <= c1max; ++c1)
+            for (int64_t c2 = c2lo; c2 <= c2hi; ++c2) {
+                const double a = (double)c1, b = (double)c2;
+                const double disc = a * a - 3 * b;
+                if (disc < -1e-9) continue;
+                const double sd = std::sqrt(std::max(disc, 0.0));
+                const double x1 = (-a - sd) / 3, x2 = (-a + sd) / 3;
+                if (x1 < -m - 1e-9 || x2 > m + 1e-9) continue;
+                auto f = [&](double x) { return ((x + a) * x + b) * x; };
+                n += range(std::max(-f(x1), -f(m)), std::min(-f(x2), -f(-m)));
+            }
+        return n;
+    }
+    return 0;
+}
+
 struct HostJob {
     hwc_job_t job;
     KJob kj;
@@ -415,7 +462,7 @@ int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n, uint32_t flags, co
     if (weighted) {
         const uint64_t qq = (uint64_t)jb.q * jb.q;
         kj.method = 2;
-        kj.words = 1;
+        kj.words = 2;   // the weighted instantiation of the two-level kernel
         kj.s_first = jb.first;
         kj.s_count = jb.count;
         kj.first = 0;
@@ -457,6 +504,8 @@ int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n, uint32_t flags, co
 uint32_t hash_capacity(uint32_t g, uint32_t q, uint64_t count, uint32_t scale)
 {
     uint64_t bound = std::min<uint64_t>(count, hasse_weil_box(g, q));
+    const uint64_t weil = weil_poly_bound(g, q);
+    if (weil) bound = std::min(bound, weil);
     uint32_t cap = next_pow2(std::max<uint64_t>(256, 2 * bound * scale));
     return std::min<uint32_t>(cap, 1u << 28);
 }

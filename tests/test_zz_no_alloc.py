@@ -74,7 +74,7 @@ def test_noalloc_matches_count_on_calls_in_a_row():
 def test_noalloc_rejects_jobs_beyond_its_scratch():
     import torch
     cache = {}
-    spec = JobSpec(3, 27, MONIC_NOSUB, 7, 0, 10_000_000)   # box of 3.4e7 tuples
+    spec = JobSpec(3, 27, MONIC_NOSUB, 7, 0, 10_000_000)   # up to 4.6e5 distinct tuples
     with pytest.raises(hwc.HwcError) as e:
         _noalloc(spec, cache)
     assert e.value.code == hwc.ERR_TOO_LARGE
