@@ -268,17 +268,33 @@ def _strip_comments(text: str) -> str:
     return " ".join(text.split())
 
 
-def kernel_source_hash() -> str:
-    """Hash of the count kernels' device sources (the .cuh headers and the
-    per-degree instantiation files) with comments and white space removed: a
-    traffic figure stays valid across comment-only edits and host-side
-    changes, and lapses on any change of kernel code."""
-    h = hashlib.sha256()
+# the instantiation files of each profiled kernel; the hash follows their
+# local #include lines
+KERNEL_SOURCES = {"k_fan2_persistent": ["fan2_a.cu", "fan2_b.cu", "fan2_wa.cu", "fan2_wb.cu"]}
+
+
+def kernel_source_hash(kernel: str = "k_fan2_persistent") -> str:
+    """Hash of a count kernel's device sources (its instantiation files and
+    every header they include, transitively) with comments and white space
+    removed: a traffic figure stays valid across comment-only edits, host-side
+    changes and changes to other kernels, and lapses on any change of this
+    kernel's code."""
+    import re
     src = os.path.join(ROOT, "paper_1805_11991_gb300", "csrc")
-    for f in sorted(os.listdir(src)):
-        if f.endswith(".cuh") or (f.endswith(".cu") and f.startswith(("fan2_", "fanout_", "horner_"))):
-            with open(os.path.join(src, f)) as fh:
-                h.update(f.encode() + b"\0" + _strip_comments(fh.read()).encode())
+    todo = [os.path.join(src, f) for f in KERNEL_SOURCES[kernel]]
+    seen = set()
+    while todo:
+        path = os.path.normpath(todo.pop())
+        if path in seen or not os.path.exists(path):
+            continue
+        seen.add(path)
+        with open(path) as fh:
+            for inc in re.findall(r'#include\s+"([^"]+)"', fh.read()):
+                todo.append(os.path.join(os.path.dirname(path), inc))
+    h = hashlib.sha256()
+    for path in sorted(seen):
+        with open(path) as fh:
+            h.update(os.path.relpath(path, ROOT).encode() + b"\0" + _strip_comments(fh.read()).encode())
     return h.hexdigest()[:16]
 
 
