@@ -10,7 +10,9 @@ launch replayed from a CUDA graph (clear, count, compact).
 value  = point evaluations of square-free members per second, device-timed
          (CUDA events on the launch stream, L2 flushed between steps);
 e2e    = the same through the public C ABI with host results (descriptor
-         upload from pinned memory, launch, histogram copy-back and sort);
+         upload from pinned memory, launch, histogram copy-back and sort;
+         two batches alternate, the host sorting one step's histograms while
+         the GPU runs the next);
 plain  = the same jobs with one launch per job (no persistent queue, no graph).
 At one GPU the line also carries, each with its own device times:
   config3 = the mixed-q workload (g=2, every odd prime power q < 64 plus
@@ -517,17 +519,29 @@ def main():
     barrier()
     plain_ms, plain_kms = _timed(plain, args.steps, stream, flush)
 
-    # e2e through the public API: launch + copy back + sort every job's histogram
+    # e2e through the public API: every step uploads its descriptors, launches,
+    # copies every job's histogram back and sorts it on the host.  Two batches
+    # of the same jobs alternate, so that the host reads one step's histograms
+    # while the GPU runs the next.
     e2e_steps = max(3, args.steps // 2)
+    other = hwc.Batch(hjobs, flags=hwc.FLAG_GRAPH | tune)
+    other.launch(stream)
+    for i in range(len(jobs)):
+        other.result(i)
+    pair = (batched, other)
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        batched.launch(stream)
+    pair[0].launch(stream)
+    for step in range(e2e_steps):
+        if step + 1 < e2e_steps:
+            pair[(step + 1) % 2].launch(stream)   # queued behind this step
+        cur = pair[step % 2]
         for i in range(len(jobs)):
-            batched.result(i)
+            cur.result(i)
     e2e_s = time.perf_counter() - t0
     h2d, d2h = batched.io_bytes()
+    other.close()
 
     all_units, all_members = units, members
     if dist is not None:

@@ -353,9 +353,9 @@ int hwc_curve_count(uint32_t q, uint32_t k, uint32_t d, uint64_t n, const uint32
  *    sorted); n_out[3] = number of entries, square-free members, members
  *    examined.  More than max_entries entries gives HWC_ERR_TOO_LARGE.
  *  - The first call on a device sets the library up for it (the device
- *    address of the array, kernel attributes); make that first call before
- *    any stream capture.  Synchronous on `stream` (it waits to report
- *    overflow).
+ *    address of the array, kernel attributes).  Synchronous on `stream`: it
+ *    waits to report overflow, so it cannot be called inside a stream
+ *    capture.
  *  - Every call shares the one array and clears it first, so calls that
  *    overlap on the GPU (other streams, other host threads) race: run them
  *    one after another. */
