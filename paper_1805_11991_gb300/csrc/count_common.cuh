@@ -387,7 +387,13 @@ __device__ void stage_job(const KJob &J, uint8_t *smem)
             const uint32_t L = J.L[k];
             const uint32_t *rs = reinterpret_cast<const uint32_t *>(J.rows[k]);
             uint32_t *rd = reinterpret_cast<uint32_t *>(smem + J.row_off[k]);
-            if (J.method == 2) {   // rows[i mod L] for i < L + 8, then y = 0 (row L of the table)
+            if (J.method == 2 && J.row16[k]) {   // int16 rows: q <= 15 digit bits, the flag (bit 31) in bit 15
+                int16_t *rd16 = reinterpret_cast<int16_t *>(rd);
+                for (uint32_t i = threadIdx.x; i <= L + kFan2ZeroRow; i += blockDim.x) {
+                    const uint32_t v = rs[i < L ? i : (i < L + kFan2ZeroRow ? (i - L) % L : L)];
+                    rd16[i] = (int16_t)(uint16_t)((v & 0x7FFFu) | ((v >> 16) & 0x8000u));
+                }
+            } else if (J.method == 2) {   // rows[i mod L] for i < L + 8, then y = 0 (row L of the table)
                 for (uint32_t i = threadIdx.x; i <= L + kFan2ZeroRow; i += blockDim.x)
                     rd[i] = rs[i < L ? i : (i < L + kFan2ZeroRow ? (i - L) % L : L)];
             } else {

@@ -191,8 +191,8 @@ __device__ __forceinline__ void queue_flagged(const uint32_t (&a)[8], const uint
 // The row's top bit is counted too, in a position no member reads.
 // GEN: points outside okm are dropped, and u may be 0.  QUEUE: queue the
 // flagged points (fields whose zero digits are not counted directly).
-template <bool GEN, bool QUEUE, class Tab>
-__device__ __forceinline__ void fan2_block(const Tab T, const uint32_t *__restrict__ rows, const uint32_t *Us,
+template <bool GEN, bool QUEUE, class Tab, class RowT>
+__device__ __forceinline__ void fan2_block(const Tab T, const RowT *__restrict__ rows, const uint32_t *Us,
                                            uint32_t L, uint32_t lb, bool b0, uint32_t okm, uint16_t *rq,
                                            uint32_t &qn, uint32_t (&a)[8])
 {
@@ -214,7 +214,7 @@ __device__ __forceinline__ void fan2_block(const Tab T, const uint32_t *__restri
     }
     // all 8 row loads before any queue store (a store may alias later loads)
 #pragma unroll
-    for (int v = 0; v < 8; ++v) a[v] = rows[ly[v]];
+    for (int v = 0; v < 8; ++v) a[v] = (uint32_t)(int32_t)rows[ly[v]];   // int16 rows: the flag fills bits 15..31
 #pragma unroll
     for (int v = 0; v < 8; ++v)
         if (GEN && !((okm >> v) & 1u)) a[v] = 0u;
@@ -227,8 +227,8 @@ __device__ __forceinline__ void fan2_block(const Tab T, const uint32_t *__restri
 // fan-out row per point, as in fan2_block, with the per-point log x folded
 // into d.  u = 0 (GEN only) is staged as U >= L and D = -log x, where
 // y_b = b x.
-template <bool GEN, bool QUEUE, class Tab>
-__device__ __forceinline__ void fan2_block_reps(const Tab T, const uint32_t *__restrict__ rows, const uint32_t *Us,
+template <bool GEN, bool QUEUE, class Tab, class RowT>
+__device__ __forceinline__ void fan2_block_reps(const Tab T, const RowT *__restrict__ rows, const uint32_t *Us,
                                                 const uint32_t *Ds, uint32_t L, uint32_t lam_b, bool b0,
                                                 uint32_t okm, uint16_t *rq, uint32_t &qn, uint32_t (&a)[8])
 {
@@ -257,7 +257,7 @@ __device__ __forceinline__ void fan2_block_reps(const Tab T, const uint32_t *__r
         }
     }
 #pragma unroll
-    for (int v = 0; v < 8; ++v) a[v] = rows[ly[v]];
+    for (int v = 0; v < 8; ++v) a[v] = (uint32_t)(int32_t)rows[ly[v]];   // int16 rows: the flag fills bits 15..31
 #pragma unroll
     for (int v = 0; v < 8; ++v)
         if (GEN && !((okm >> v) & 1u)) a[v] = 0u;
@@ -272,7 +272,7 @@ __device__ __forceinline__ void fan2_block_reps(const Tab T, const uint32_t *__r
 // J.reps[k] (J.npts[k] of them), else every x = alpha^j, j < L.  A zero of
 // f_{b,c} adds zw to its accumulator (1, or 1 + 2^s to keep the field's zeros
 // apart in bits s..).
-template <int D, bool TRIPLE, bool PAD, int KF, bool REPS>
+template <int D, bool TRIPLE, bool PAD, int KF, bool REPS, class RowT = uint32_t>
 __device__ __forceinline__ void group2_field(const KJob &J, int k, const uint8_t *smem, const HChain<D> *gH,
                                              const uint32_t *glam, uint32_t nz, uint32_t *Us, uint32_t *Ds,
                                              uint16_t *acc, uint16_t *acc_row, uint16_t *rq, int lane, bool role,
@@ -282,7 +282,7 @@ __device__ __forceinline__ void group2_field(const KJob &J, int k, const uint8_t
     const TabP<PAD> T{reinterpret_cast<const uint16_t *>(smem) + J.tab_off[k]};
     const uint32_t L = J.L[k];
     const uint32_t bar = J.barrett[k];
-    const uint32_t *rows = reinterpret_cast<const uint32_t *>(smem + J.row_off[k]);   // [L + 9]
+    const RowT *rows = reinterpret_cast<const RowT *>(smem + J.row_off[k]);   // [L + 9]
     const uint8_t *zdig = smem + J.zdig_off[k];
     const uint32_t zdiv = J.zdiv[k];
     const uint32_t *coefk = reinterpret_cast<const uint32_t *>(smem) + J.coef_off[k];
@@ -430,6 +430,17 @@ __device__ __forceinline__ void group2_field_tabs(const KJob &J, int k, bool tri
 #define HWC_G2F(TRI, PAD, REPS)                                                                             \
     group2_field<D, TRI, PAD, KF, REPS>(J, k, smem, gH, glam, nz, Us, Ds, acc, acc_row, rq, lane, role, b, s, S, \
                                         zw)
+    if constexpr (D >= 9 && KF == 0) {   // g = 4: int16 rows (doubled Zech layout, orbit points)
+        if (J.row16[k]) {
+            if (J.tab_pad[k])
+                group2_field<D, false, true, 0, true, int16_t>(J, k, smem, gH, glam, nz, Us, Ds, acc, acc_row, rq,
+                                                               lane, role, b, s, S, zw);
+            else
+                group2_field<D, false, false, 0, true, int16_t>(J, k, smem, gH, glam, nz, Us, Ds, acc, acc_row, rq,
+                                                                lane, role, b, s, S, zw);
+            return;
+        }
+    }
     if (KF != 1 && J.reps[k]) {   // field 1 (KF = 1) takes every point
         if (J.tab_pad[k]) {
             if (tri) HWC_G2F(true, true, true);

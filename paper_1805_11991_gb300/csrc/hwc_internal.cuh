@@ -157,6 +157,7 @@ struct KJob {
     const void *rows[kMaxG];          // d_rows32 / d_rows64
     const uint8_t *zdig[kMaxG];
     uint32_t row_off[kMaxG];          // byte offset of the rows in smem
+    uint32_t row16[kMaxG];            // method 2: 1 = the field's rows staged as int16 (q <= 15, bit 15 the flag)
     uint32_t zdig_off[kMaxG];         // byte offset of zdig in smem
     uint32_t zdiv[kMaxG];             // ceil(2^32 / (L/(q-1))): l / s by a high multiply
     uint32_t warp_off, warp_bytes;    // per-warp scratch in smem (method 2)
@@ -298,7 +299,7 @@ __host__ __device__ inline Fan2Layout fan2_layout(uint32_t q, bool dense)
 }
 inline uint32_t fan2_warp_bytes(uint32_t q, bool dense) { return fan2_layout(q, dense).bytes; }
 // launch shape of the two-level kernel for jobs with these smem needs: the
-// block (4, 8, 16 or 24 warps) that keeps most warps resident; *smem receives the
+// block (4, 8, 12, 16 or 24 warps) that keeps most warps resident; *smem receives the
 // dynamic shared memory of that block
 struct Fan2Need {
     uint32_t warp_off, warp_bytes;

@@ -141,8 +141,12 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit, bool no_triple)
         if (pad[k]) n += 2 * ((n + 63) / 64);
         return ((n + 7) / 8) * 8;
     };
+    // the two-level kernel for g = 4 and q <= 15 may stage a field's rows as
+    // int16 (q digit bits, the flag in bit 15) when the u32 rows leave too
+    // little room; such a field takes the doubled Zech layout and its orbit points
+    uint32_t r16[kMaxG] = {0, 0, 0, 0};
     auto row_bytes = [&](uint32_t k) -> uint64_t {
-        return j.method == 2 ? 4ull * (j.L[k] + kFan2ZeroRow + 1) : 4ull * j.words * (j.L[k] + 1);
+        return j.method == 2 ? (r16[k] ? 2ull : 4ull) * (j.L[k] + kFan2ZeroRow + 1) : 4ull * j.words * (j.L[k] + 1);
     };
     auto fan_bytes = [&](void) -> uint64_t {
         if (j.method == 0) return 0;
@@ -158,6 +162,18 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit, bool no_triple)
         for (uint32_t k = 0; k < j.g; ++k) u16 += words(k);
         return u16 * 2 + 4ull * j.g * ((j.q + 3) / 4) * 4 + fan_bytes();
     };
+    // int16 rows, largest field first, while that makes room for 16 warps
+    if (j.method == 2 && j.g == 4 && j.q <= 15) {
+        const uint64_t extra = (uint64_t)(16 - kFan2WarpsHost) * fan2_warp_bytes(j.q, false);
+        while (bytes_for() + extra > smem_limit) {
+            int big = -1;
+            for (uint32_t k = 0; k < j.g; ++k)
+                if (!r16[k] && j.reps[k] && j.zech2[k] && (big < 0 || row_bytes(k) > row_bytes(big))) big = (int)k;
+            if (big < 0) break;
+            r16[big] = 1;
+            kind[big] = kTabDoubleSmem;
+        }
+    }
     // the two-level kernel reads its Zech tables only in the shared chain: give
     // up tripled tables, largest first, while that makes room for 16 warps
     if (j.method == 2) {
@@ -187,6 +203,7 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit, bool no_triple)
     for (uint32_t k = 0; k < kMaxG; ++k) {
         j.tab_kind[k] = k < j.g ? kind[k] : kTabDoubleGlobal;
         j.tab_pad[k] = (k < j.g && kind[k] != kTabDoubleGlobal && kind[k] != kTab17Smem) ? pad[k] : 0u;
+        j.row16[k] = k < j.g ? r16[k] : 0u;
         j.tab_off[k] = off;
         // 17-bit layout: L + 1 low halves (even count), then the high-bit plane
         j.tab_hi_off[k] = off + (k < j.g ? ((j.L[k] + 2u) & ~1u) : 0u);
@@ -750,7 +767,7 @@ int hwc::choose_shape_fan2(int D, const Fan2Need *needs, size_t n, LaunchShape *
     const int sms = device_sm_count();
     const uint32_t limit = device_smem_optin() - 4096;
     int best_warps = -1;
-    for (int block : {768, 512, 256, 128}) {
+    for (int block : {768, 512, 384, 256, 128}) {
         if (warps > 0 && block != 32 * warps) continue;   // the tuned block
         const uint32_t W = (uint32_t)block / 32;
         uint32_t need = 0;

@@ -104,9 +104,18 @@ def config3_q293_slice():
     return [JobSpec(2, 293, MONIC_NOSUB_SAMPLED, 5, 0, 1 << 18, seed=7, sample_count=1 << 24)]
 
 
+def config5_q13_slice():
+    """2^20 members from the middle of the full g=4 q=13 degree-9 family (6,205
+    groups of q^2 members): the small case used for profiles of the two-level
+    kernel with the int16 rows of F_{13^4} (the same code as the weighted run
+    of configuration 5's q=13 job, without the weights)."""
+    return [JobSpec(4, 13, MONIC_NOSUB, 9, 13 ** 8 // 2, 1 << 20)]
+
+
 CONFIGS = {"config1": config1, "config2": config2, "config3": config3, "config4": config4,
            "config5": config5, "config2_q31d5": config2_q31d5, "config2_q31d6": config2_q31d6,
-           "config4_q27_slice": config4_q27_slice, "config3_q293_slice": config3_q293_slice}
+           "config4_q27_slice": config4_q27_slice, "config3_q293_slice": config3_q293_slice,
+           "config5_q13_slice": config5_q13_slice}
 
 
 def poisson_arrivals(n: int, rate_per_s: float, seed: int = 11) -> np.ndarray:
