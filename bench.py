@@ -332,7 +332,8 @@ def serve_leg(hwc, jobs, batched_results, batched_evals_per_s, n_requests, load,
         reqs += [(j, r) for r in split_job(spec, max(1, round(w / target)))]
     order = np.random.default_rng(seed).permutation(len(reqs))
     reqs = [reqs[i] for i in order]
-    req_evals = [r.n() * evals_per_member(r) for _, r in reqs]
+    # a window of a densely drawn sample counts the draws landing in it
+    req_evals = [r.drawn() * evals_per_member(r) for _, r in reqs]
     mean_service_s = (sum(req_evals) / len(reqs)) / batched_evals_per_s
     arrivals = poisson_arrivals(len(reqs), load / mean_service_s, seed=seed)
     srv = hwc.Server()
@@ -366,7 +367,8 @@ def serve_leg(hwc, jobs, batched_results, batched_evals_per_s, n_requests, load,
     return {"value": sqf / (t_end - t0), "unit": UNIT, "requests": len(reqs),
             "arrival_rate_per_s": load / mean_service_s, "offered_load": load,
             "p50_ms": p(0.50), "p99_ms": p(0.99), "max_ms": lat[-1], "wall_s": t_end - t0,
-            "arrivals": "Poisson, seed %d; requests: every job cut into slices of equal work, shuffled" % seed,
+            "arrivals": "Poisson, seed %d; requests: every job cut into slices of equal work (a densely drawn "
+                        "sample into windows of members with the draws landing in them), shuffled" % seed,
             "matches_batched": bool(same)}
 
 

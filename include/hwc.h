@@ -82,6 +82,22 @@ extern "C" {
  *                        a_k -> (-1)^k a_k.  The histogram then equals the one
  *                        over every square-free f of degree d (eq. 1.2). */
 #define HWC_FAM_REDUCED 3u
+/*  HWC_FAM_MONIC_NOSUB_SAMPLED_WINDOW
+ *                        the draws of HWC_FAM_MONIC_NOSUB_SAMPLED (samples
+ *                        0 <= j < sample_count, seed) that land in a window of
+ *                        member indices: the job's [first, first + count)
+ *                        names members of HWC_FAM_MONIC_NOSUB (q^(d-1) of
+ *                        them), and each member of the window is counted as
+ *                        often as the samples draw it.  Disjoint windows
+ *                        covering the family add up to the whole sampled
+ *                        family, which lets a request stream cut a densely
+ *                        drawn family into pieces of equal work without
+ *                        losing the whole-family kernel.  Only that kernel
+ *                        runs it: q <= 31, sample_count >= q^(d-1) / 32 and
+ *                        < 2^27, tables in shared memory; otherwise, and for
+ *                        hwc_count_members, HWC_ERR_ARG.  No counterpart in
+ *                        the paper (serving). */
+#define HWC_FAM_MONIC_NOSUB_SAMPLED_WINDOW 4u
 
 typedef struct {
     uint32_t kind;          /* HWC_FAM_*                                   */

@@ -57,13 +57,14 @@ __global__ void k_compact(const KJob *__restrict__ jobs, uint32_t n_jobs)
 
 // multiplicities of the sampled members (the choice of f in Algorithm 1 for
 // a sampled family, hwc.h): sample j draws member floor(z_j * fam / 2^64)
+// (members w_first <= idx < w_first + w_n kept, at w[idx - w_first])
 __global__ void k_sample_weights(uint64_t seed, uint64_t s_first, uint64_t s_count, uint64_t fam,
-                                 uint32_t *__restrict__ w)
+                                 uint64_t w_first, uint64_t w_n, uint32_t *__restrict__ w)
 {
     for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < s_count;
          j += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t idx = __umul64hi(splitmix64_at(seed, s_first + j), fam);
-        atomicAdd(w + idx, 1u);
+        if (idx - w_first < w_n) atomicAdd(w + (idx - w_first), 1u);   // unsigned: idx >= w_first too
     }
 }
 
@@ -72,11 +73,12 @@ __global__ void k_sample_weights(uint64_t seed, uint64_t s_first, uint64_t s_cou
 int launch_sample_weights(const KJob &kj, cudaStream_t s)
 {
     if (!kj.mweight) return HWC_OK;
-    HWC_CUDA_TRY(cudaMemsetAsync(kj.mweight, 0, kj.fam_mz * sizeof(uint32_t), s));
+    HWC_CUDA_TRY(cudaMemsetAsync(kj.mweight, 0, kj.w_n * sizeof(uint32_t), s));
     if (kj.s_count) {
         const uint64_t want = (kj.s_count + 255) / 256;
         const unsigned grid = (unsigned)std::min<uint64_t>(want, (uint64_t)device_sm_count() * 8);
-        k_sample_weights<<<grid, 256, 0, s>>>(kj.seed, kj.s_first, kj.s_count, kj.fam_mz, kj.mweight);
+        k_sample_weights<<<grid, 256, 0, s>>>(kj.seed, kj.s_first, kj.s_count, kj.fam_mz, kj.w_first, kj.w_n,
+                                              kj.mweight);
         HWC_CUDA_TRY(cudaGetLastError());
     }
     return HWC_OK;

@@ -746,7 +746,7 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
             const uint32_t m = t * 32 + lane;
             const uint64_t idx = base + m;
             bool v = m < qq && idx >= J.first && idx < J.first + J.count;
-            const uint32_t w = v ? J.mweight[idx] : 0u;   // multiplicity among the samples (0: not drawn)
+            const uint32_t w = v ? J.mweight[idx - J.w_first] : 0u;   // multiplicity among the samples (0: not drawn)
             v = v && w != 0;
             const bool sq = v && ((sqfw[t] >> lane) & 1u);
             const unsigned vm = __ballot_sync(0xFFFFFFFFu, v);
@@ -893,7 +893,7 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
                         const int i1 = (int)k1 - 32768 + J.dense_b1;
                         const int i2 = G == 2 ? a + J.dense_b2 : 0;
                         uint32_t w = 1;
-                        if constexpr (W) w = J.mweight[base + m];
+                        if constexpr (W) w = J.mweight[base + m - J.w_first];
                         if (i1 >= 0 && i1 <= 2 * J.dense_b1 && i2 >= 0 && i2 <= 2 * J.dense_b2)
                             atomicAdd(&dense[(uint32_t)i1 * J.dense_w2 + (uint32_t)i2], w);
                         else   // outside the Hasse-Weil box: not for a smooth curve
@@ -932,7 +932,7 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
             const unsigned peers = __match_any_sync(smask, key);
             // equal keys counted once: the peers' members, or their multiplicities
             uint32_t cnt;
-            if constexpr (W) cnt = __reduce_add_sync(peers, J.mweight[base + m]);
+            if constexpr (W) cnt = __reduce_add_sync(peers, J.mweight[base + m - J.w_first]);
             else cnt = __popc(peers);
             if (lane == __ffs(peers) - 1) hist_insert(J, key, cnt);
         }

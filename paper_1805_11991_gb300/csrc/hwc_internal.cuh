@@ -184,9 +184,11 @@ struct KJob {
     // mweight[i] = how often member i of HWC_FAM_MONIC_NOSUB was drawn by the
     // samples [s_first, s_first + s_count) (launch_sample_weights); the kernel
     // counts member i with that weight (0: not drawn).  first / count then
-    // cover the whole family.  Null: every member in range has weight 1.
+    // cover the whole family, or the window of HWC_FAM_MONIC_NOSUB_SAMPLED_WINDOW.
+    // Null: every member in range has weight 1.
     uint32_t *mweight;
     uint64_t s_first, s_count;
+    uint64_t w_first, w_n;            // mweight[i - w_first] for members w_first <= i < w_first + w_n
 };
 
 // launch helpers (count_kernels.cu)
@@ -224,7 +226,10 @@ struct TuneChoice {
 bool layout_job_smem(KJob &j, uint32_t smem_limit, bool no_triple = false);
 // a sampled job counted by the two-level kernel over its whole family, with
 // the samples' multiplicities as weights (KJob::mweight)
-inline bool needs_weights(const KJob &kj) { return kj.kind == HWC_FAM_MONIC_NOSUB_SAMPLED && kj.method == 2; }
+inline bool needs_weights(const KJob &kj)
+{
+    return (kj.kind == HWC_FAM_MONIC_NOSUB_SAMPLED || kj.kind == HWC_FAM_MONIC_NOSUB_SAMPLED_WINDOW) && kj.method == 2;
+}
 // fill_kjob flag (internal): keep sampled families on the per-member kernel
 // (per-sample outputs need the members in sample order)
 constexpr uint32_t kFlagNoWeights = 1u << 31;

@@ -63,6 +63,10 @@ static int family_size(uint32_t q, const hwc_family_t *fam, uint64_t *n)
         if (!upow(q, d - 1, &v)) return set_error(HWC_ERR_TOO_LARGE, "family size overflows");
         v = fam->sample_count;
         break;
+    case HWC_FAM_MONIC_NOSUB_SAMPLED_WINDOW:   // windows name members of the enumerated family
+        if (!upow(q, d - 1, &v)) return set_error(HWC_ERR_TOO_LARGE, "family size overflows");
+        if (fam->sample_count == 0) return set_error(HWC_ERR_ARG, "windowed sampled family without samples");
+        break;
     case HWC_FAM_REDUCED: {   // patterns A, B and (i, j) of Sec. 1.2 (see hwc.h)
         if (d % p == 0) return set_error(HWC_ERR_ARG, "reduced family needs p=%u not dividing d=%u", p, d);
         v = 2ull * (q - 1);
@@ -432,7 +436,9 @@ int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n, uint32_t flags, co
         if (off + 4 * jb.g + 1 > 63) return set_error(HWC_ERR_TOO_LARGE, "lambda key needs %u bits", off + 4 * jb.g + 1);
     }
     // enumerated families with q <= 63: groups of q members share all but c_0
+    const bool window = jb.family.kind == HWC_FAM_MONIC_NOSUB_SAMPLED_WINDOW;
     const bool fan = !(flags & (HWC_FLAG_HORNER | HWC_FLAG_LAMBDA)) && jb.family.kind != HWC_FAM_MONIC_NOSUB_SAMPLED &&
+                     !window &&
                      jb.family.kind != HWC_FAM_REDUCED && jb.q <= 63 &&
                      !(tc && tc->method == 0);
     const bool no_triple = tc && tc->no_triple;
@@ -476,6 +482,25 @@ int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n, uint32_t flags, co
                           !(flags & (HWC_FLAG_HORNER | HWC_FLAG_FAN1 | HWC_FLAG_LAMBDA | kFlagNoWeights)) &&
                           !(tc && tc->method >= 0 && tc->method != 2) && jb.count >= kj.fam_mz / 32 &&
                           jb.count < (1ull << 27) && kj.fam_mz <= (1ull << 32);
+    if (window) {   // the draws of the whole sample in a window of members: the weighted kernel only
+        const uint64_t qq = (uint64_t)jb.q * jb.q;
+        const uint64_t sc = jb.family.sample_count;
+        if (jb.q > 31 || (flags & (HWC_FLAG_HORNER | HWC_FLAG_FAN1 | HWC_FLAG_LAMBDA | kFlagNoWeights)) ||
+            (tc && tc->method >= 0 && tc->method != 2) || sc < kj.fam_mz / 32 || sc >= (1ull << 27) ||
+            kj.fam_mz > (1ull << 32))
+            return set_error(HWC_ERR_ARG, "a windowed sampled family runs only on the whole-family kernel "
+                                          "(q <= 31, at least one draw per 32 members, fewer than 2^27 draws)");
+        kj.method = 2;
+        kj.words = 2;
+        kj.s_first = 0;
+        kj.s_count = sc;
+        kj.w_first = jb.first;
+        kj.w_n = jb.count;
+        kj.first_group = jb.first / qq;
+        kj.n_tiles = jb.count ? (jb.first + jb.count - 1) / qq - kj.first_group + 1 : 0;
+        if (layout_job_smem(kj, limit, no_triple)) return HWC_OK;
+        return set_error(HWC_ERR_ARG, "the tables of a windowed sampled family do not fit in shared memory");
+    }
     if (weighted) {
         const uint64_t qq = (uint64_t)jb.q * jb.q;
         kj.method = 2;
@@ -484,12 +509,15 @@ int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n, uint32_t flags, co
         kj.s_count = jb.count;
         kj.first = 0;
         kj.count = kj.fam_mz;
+        kj.w_first = 0;
+        kj.w_n = kj.fam_mz;
         kj.first_group = 0;
         kj.n_tiles = kj.fam_mz / qq;
         if (layout_job_smem(kj, limit, no_triple)) return HWC_OK;
         kj.first = jb.first;   // tables do not fit: per-member Horner over the samples
         kj.count = jb.count;
         kj.s_first = kj.s_count = 0;
+        kj.w_first = kj.w_n = 0;
         kj.first_group = 0;
         kj.method = 0;
         kj.words = 0;
@@ -868,7 +896,7 @@ static int batch_create_impl(const hwc_job_t *jobs, size_t n, uint32_t flags, ui
         if ((rc = dalloc(b, &kj.hkeys, cap)) || (rc = dalloc(b, &kj.hcounts, cap)) ||
             (rc = dalloc(b, &kj.stats, 4)) || (rc = dalloc(b, &kj.out_keys, cap)) ||
             (rc = dalloc(b, &kj.out_counts, cap)) || (rc = dalloc(b, &kj.n_out, 1)) ||
-            (needs_weights(kj) && (rc = dalloc(b, &kj.mweight, kj.fam_mz)))) {
+            (needs_weights(kj) && (rc = dalloc(b, &kj.mweight, kj.w_n)))) {
             batch_release(b);
             return rc;
         }

@@ -156,7 +156,7 @@ int admit(hwc_server *s, Request *r)
     KJob &kj = r->kj;
     const uint64_t cap = kj.hmask + 1ull;
     const uint64_t bytes[8] = {8 * cap, 8 * cap, 8 * 4, 8 * cap, 8 * cap, 8, sizeof(KJob),
-                               needs_weights(kj) ? 4 * kj.fam_mz : 0};
+                               needs_weights(kj) ? 4 * kj.w_n : 0};
     void *ptrs[8];
     int rc = ralloc_all(s, r, bytes, ptrs, 8);
     if (rc) return rc;
@@ -470,7 +470,7 @@ extern "C" int hwc_serve_submit(hwc_server_t *s, const hwc_job_t *job, uint64_t 
         return rc;
     }
     r->kj.hmask = hash_capacity(r->kj.g, r->kj.q, job->count, 1) - 1;
-    r->bytes = 32ull * (r->kj.hmask + 1ull) + 4096 + (needs_weights(r->kj) ? 4 * r->kj.fam_mz : 0);
+    r->bytes = 32ull * (r->kj.hmask + 1ull) + 4096 + (needs_weights(r->kj) ? 4 * r->kj.w_n : 0);
     {
         std::lock_guard<std::mutex> lk(s->mu);
         for (uint32_t k = 1; k <= job->g; ++k)

@@ -77,7 +77,8 @@ TuneChoice make(int method, int warps, bool no_triple)
 std::vector<TuneChoice> candidates(const hwc_job_t &jb, uint32_t flags)
 {
     std::vector<TuneChoice> v;
-    const bool sampled = jb.family.kind == HWC_FAM_MONIC_NOSUB_SAMPLED || jb.family.kind == HWC_FAM_REDUCED;
+    const bool sampled = jb.family.kind == HWC_FAM_MONIC_NOSUB_SAMPLED || jb.family.kind == HWC_FAM_REDUCED ||
+                         jb.family.kind == HWC_FAM_MONIC_NOSUB_SAMPLED_WINDOW;
     if (sampled || (flags & (HWC_FLAG_HORNER | HWC_FLAG_LAMBDA)) || jb.q > 63) return {make(0, 0, false)};
     if (jb.q <= 31 && !(flags & HWC_FLAG_FAN1)) {
         v.push_back(make(2, 0, false));   // the default: most resident warps

@@ -20,6 +20,7 @@ ERR_ARG, ERR_RANGE, ERR_TOO_LARGE, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_BUSY, E
 MAX_Q = 262144
 
 FAM_ALL_DEG, FAM_MONIC_NOSUB, FAM_MONIC_NOSUB_SAMPLED, FAM_REDUCED = 0, 1, 2, 3
+FAM_MONIC_NOSUB_SAMPLED_WINDOW = 4
 FLAG_PLAIN, FLAG_GRAPH, FLAG_HORNER, FLAG_NO_TUNE, FLAG_TIMING, FLAG_FAN1 = 0x1, 0x2, 0x4, 0x8, 0x10, 0x20
 FLAG_ALL_POINTS = 0x40
 FLAG_LAMBDA = 0x80

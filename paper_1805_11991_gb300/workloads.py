@@ -12,6 +12,7 @@ from dataclasses import dataclass
 import numpy as np
 
 ALL_DEG, MONIC_NOSUB, MONIC_NOSUB_SAMPLED = 0, 1, 2
+MONIC_NOSUB_SAMPLED_WINDOW = 4   # the draws of a sampled family in a window of members
 
 # odd prime powers below 64
 ODD_PRIME_POWERS_BELOW_64 = [3, 5, 7, 9, 11, 13, 17, 19, 23, 25, 27, 29, 31, 37, 41, 43, 47, 49,
@@ -32,12 +33,26 @@ class JobSpec:
     def family_members(self) -> int:
         if self.kind == ALL_DEG:
             return (self.q - 1) * self.q ** self.degree
-        if self.kind == MONIC_NOSUB:
+        if self.kind in (MONIC_NOSUB, MONIC_NOSUB_SAMPLED_WINDOW):
             return self.q ** (self.degree - 1)
         return self.sample_count
 
     def n(self) -> int:
         return self.family_members() - self.first if self.count < 0 else self.count
+
+    def drawn(self) -> float:
+        """Members the job counts: the range, or for a window of a sampled
+        family the expected number of draws landing in it."""
+        if self.kind == MONIC_NOSUB_SAMPLED_WINDOW:
+            return self.sample_count * self.n() / self.family_members()
+        return float(self.n())
+
+    def whole_family_draws(self) -> bool:
+        """A sampled family drawn densely enough for the whole-family kernel
+        (q <= 31, at least one draw per 32 members, fewer than 2^27 draws)."""
+        fam = self.q ** (self.degree - 1)
+        return (self.kind == MONIC_NOSUB_SAMPLED and self.q <= 31 and self.sample_count < (1 << 27)
+                and 32 * self.n() >= fam)
 
     def nominal_evals_per_member(self) -> int:
         """Points x in F_{q^k}, k = 1..g, each member is evaluated at."""
@@ -129,6 +144,16 @@ def split_job(job: JobSpec, parts: int):
     shards)."""
     n = job.n()
     out = []
+    if job.whole_family_draws() and job.first == 0 and n == job.sample_count:
+        # a densely drawn sample: windows of the enumerated family, each with
+        # the draws that land in it (their union is the whole sample)
+        fam = job.q ** (job.degree - 1)
+        for i in range(parts):
+            a, b = (fam * i) // parts, (fam * (i + 1)) // parts
+            if b > a:
+                out.append(JobSpec(job.g, job.q, MONIC_NOSUB_SAMPLED_WINDOW, job.degree, a, b - a, job.seed,
+                                   job.sample_count))
+        return out
     for i in range(parts):
         a = job.first + (n * i) // parts
         b = job.first + (n * (i + 1)) // parts

@@ -49,6 +49,11 @@ def test_family_sizes_host_only():
     assert hwc.family_size(31, hwc.make_family(hwc.FAM_MONIC_NOSUB, 5)) == 31 ** 4
     assert hwc.family_size(3, hwc.make_family(hwc.FAM_ALL_DEG, 6)) == 2 * 3 ** 6
     assert hwc.family_size(293, hwc.make_family(hwc.FAM_MONIC_NOSUB_SAMPLED, 5, 7, 1 << 24)) == 1 << 24
+    # windows of a sampled family name members of the enumerated family
+    assert hwc.family_size(13, hwc.make_family(hwc.FAM_MONIC_NOSUB_SAMPLED_WINDOW, 9, 11, 1 << 26)) == 13 ** 8
+    with pytest.raises(hwc.HwcError) as e:
+        hwc.family_size(13, hwc.make_family(hwc.FAM_MONIC_NOSUB_SAMPLED_WINDOW, 9, 11, 0))
+    assert e.value.code == hwc.ERR_ARG
     with pytest.raises(hwc.HwcError) as e:
         hwc.family_size(15, hwc.make_family(hwc.FAM_MONIC_NOSUB, 5))
     assert e.value.code == hwc.ERR_ARG
