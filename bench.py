@@ -78,7 +78,7 @@ def evals_per_member(spec: JobSpec) -> int:
     return spec.nominal_evals_per_member()
 
 
-KERNELS = {0: "k_persistent", 1: "k_fan_persistent", 2: "k_fan2_persistent"}
+KERNELS = {0: "k_persistent", 1: "k_fan_persistent", 2: "k_fan2_persistent", 3: "k_cls_persistent"}
 
 
 def chain_reads(spec: JobSpec, lo: int) -> float:
@@ -124,9 +124,16 @@ def table_reads(spec: JobSpec, n_squarefree: int, method: int) -> float:
         point, the chain over c_2..c_d, one Zech addition per c_1 != 0 and
         one fan-out row per c_1: chain + 2q - 1.  A sampled family on this
         kernel is counted over every group of its family (the samples'
-        multiplicities as weights)."""
+        multiplicities as weights);
+      3, sampled members sorted by class (c_2..c_{d-2}): per tile of up to 32
+        samples of a class and point, the chain over c_2..c_d, and per
+        square-free member and point one Zech read for c_1 != 0 and one for
+        c_0 != 0 (tiles: samples / 32 + classes / 2 expected)."""
     d, q = spec.degree, spec.q
     pts = points_per_member(spec)
+    if method == 3:
+        tiles = spec.n() / 32 + q ** (d - 3) / 2
+        return n_squarefree * pts * 2 * (q - 1) / q + tiles * pts * chain_reads(spec, 2)
     if method == 2:
         members = q ** (d - 1) if spec.kind == MONIC_NOSUB_SAMPLED else spec.n()
         return members / q ** 2 * pts * (chain_reads(spec, 2) + 2 * q - 1)

@@ -282,7 +282,10 @@ int hwc_batch_result(hwc_batch_t *b, size_t i, hwc_hist_t **out);
 int hwc_batch_kernel_launches(const hwc_batch_t *b, uint32_t *n);
 /* Count kernel that job i of the batch runs: 0 per-member Horner evaluation
  * (Algorithm 1 as written), 1 fan-out over c_0 (groups of q members sharing
- * c_1..c_d), 2 fan-out over (c_1, c_0) (groups of q^2 members).  The choice
+ * c_1..c_d), 2 fan-out over (c_1, c_0) (groups of q^2 members), 3 per-member
+ * evaluation of a sampled family sorted by its high digits c_2..c_{d-2}
+ * (degrees 3..6, at least 16 samples per class on average; the samples of a
+ * class share the chain for u = sum_{i>=2} c_i x^i).  The choice
  * is made at hwc_batch_create from the family, q and the shared-memory room
  * of the field tables (HWC_FLAG_HORNER / HWC_FLAG_FAN1 restrict it). */
 int hwc_batch_job_method(const hwc_batch_t *b, size_t i, uint32_t *method);

@@ -68,7 +68,106 @@ __global__ void k_sample_weights(uint64_t seed, uint64_t s_first, uint64_t s_cou
     }
 }
 
+// Counting sort of a class-sharing job's samples by class c = idx / q^2 (the
+// digits c_2..c_{d-2} of member idx): per-class counts, then one CTA turns
+// them into class starts (cnt[c] becomes the cursor) and writes the tile list
+// (up to 32 samples of one class per tile), then every sample is placed by an
+// atomic on its class cursor, which ends at the end of the class.
+__global__ void k_cls_count(uint64_t seed, uint64_t first, uint64_t count, uint64_t fam, uint64_t q2,
+                            uint32_t *__restrict__ cnt)
+{
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < count;
+         j += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t idx = __umul64hi(splitmix64_at(seed, first + j), fam);
+        atomicAdd(cnt + idx / q2, 1u);
+    }
+}
+
+constexpr int kScanThreads = 1024;
+
+__global__ void __launch_bounds__(kScanThreads) k_cls_scan(uint32_t *__restrict__ cnt, uint32_t n_cls,
+                                                           uint2 *__restrict__ tiles, uint64_t n_tiles)
+{
+    __shared__ uint32_t s_n[kScanThreads / 32], s_t[kScanThreads / 32];
+    __shared__ uint32_t s_total;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const uint32_t per = (n_cls + kScanThreads - 1) / kScanThreads;
+    const uint32_t a = min(n_cls, tid * per), b = min(n_cls, a + per);
+    uint32_t sn = 0, st = 0;   // samples and tiles of this thread's classes
+    for (uint32_t c = a; c < b; ++c) {
+        sn += cnt[c];
+        st += (cnt[c] + 31u) / 32u;
+    }
+    // block-wide exclusive scan of (sn, st)
+    uint32_t in = sn, it = st;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t vn = __shfl_up_sync(0xFFFFFFFFu, in, o), vt = __shfl_up_sync(0xFFFFFFFFu, it, o);
+        if ((int)lane >= o) {
+            in += vn;
+            it += vt;
+        }
+    }
+    if (lane == 31) {
+        s_n[warp] = in;
+        s_t[warp] = it;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t wn = s_n[lane], wt = s_t[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t vn = __shfl_up_sync(0xFFFFFFFFu, wn, o), vt = __shfl_up_sync(0xFFFFFFFFu, wt, o);
+            if ((int)lane >= o) {
+                wn += vn;
+                wt += vt;
+            }
+        }
+        s_n[lane] = wn;   // inclusive over warps
+        s_t[lane] = wt;
+        if (lane == 31) s_total = wt;
+    }
+    __syncthreads();
+    uint32_t off = in - sn + (warp ? s_n[warp - 1] : 0u);
+    uint32_t toff = it - st + (warp ? s_t[warp - 1] : 0u);
+    for (uint32_t c = a; c < b; ++c) {
+        const uint32_t n = cnt[c];
+        cnt[c] = off;   // the class cursor starts at the class start
+        for (uint32_t r = 0; r < n; r += 32) tiles[toff++] = make_uint2(c, off + r);
+        off += n;
+    }
+    for (uint64_t t = s_total + tid; t < n_tiles; t += kScanThreads) tiles[t] = make_uint2(0xFFFFFFFFu, 0u);
+}
+
+__global__ void k_cls_scatter(uint64_t seed, uint64_t first, uint64_t count, uint64_t fam, uint64_t q2,
+                              uint32_t *__restrict__ cursor, uint32_t *__restrict__ sorted)
+{
+    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < count;
+         j += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t idx = __umul64hi(splitmix64_at(seed, first + j), fam);
+        const uint64_t c = idx / q2;
+        const uint32_t pos = atomicAdd(cursor + c, 1u);
+        sorted[pos] = (uint32_t)(idx - c * q2);   // c_0 + c_1 q
+    }
+}
+
 }  // namespace
+
+int launch_class_sort(const KJob &kj, cudaStream_t s)
+{
+    if (!kj.cls_n || !kj.count) return HWC_OK;
+    const uint64_t q2 = (uint64_t)kj.q * kj.q;
+    const uint64_t want = (kj.count + 255) / 256;
+    const unsigned grid = (unsigned)std::min<uint64_t>(want, (uint64_t)device_sm_count() * 8);
+    HWC_CUDA_TRY(cudaMemsetAsync(kj.cls_cnt, 0, (size_t)kj.cls_n * sizeof(uint32_t), s));
+    k_cls_count<<<grid, 256, 0, s>>>(kj.seed, kj.first, kj.count, kj.fam_mz, q2, kj.cls_cnt);
+    HWC_CUDA_TRY(cudaGetLastError());
+    k_cls_scan<<<1, kScanThreads, 0, s>>>(kj.cls_cnt, kj.cls_n, kj.cls_tiles, kj.n_tiles);
+    HWC_CUDA_TRY(cudaGetLastError());
+    k_cls_scatter<<<grid, 256, 0, s>>>(kj.seed, kj.first, kj.count, kj.fam_mz, q2, kj.cls_cnt, kj.cls_sorted);
+    HWC_CUDA_TRY(cudaGetLastError());
+    return HWC_OK;
+}
 
 int launch_sample_weights(const KJob &kj, cudaStream_t s)
 {
@@ -119,6 +218,11 @@ static KernelFn persistent_fn(int D, int block = 256)
     return horner_kernel(D, block > 256 ? 3 : 1);
 }
 
+static KernelFn cls_fn(int D, int block = 256)
+{
+    return D >= 3 && D <= 6 ? cls_kernel_a(D, block > 256 ? 3 : 1) : nullptr;
+}
+
 int prepare_count_kernels(void)
 {
     static std::mutex mu;
@@ -130,7 +234,7 @@ int prepare_count_kernels(void)
     const int optin = (int)device_smem_optin();
     for (int D = 3; D <= kMaxD; ++D) {
         for (KernelFn fn : {persistent_fn(D), persistent_fn(D, 768), fan_kernel(D, 1, true), fan_kernel(D, 2, true),
-                            fan2_kernel(D, false), fan2_kernel(D, true)}) {
+                            fan2_kernel(D, false), fan2_kernel(D, true), cls_fn(D), cls_fn(D, 768)}) {
             if (!fn) continue;   // no kernel for this degree and row width
             cudaFuncAttributes fa{};
             HWC_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));   // static smem counts against the limit
@@ -165,6 +269,7 @@ static KernelFn kernel_for(int D, uint32_t method, uint32_t words, bool persiste
     if (method == 2) return fan2_kernel(D, words == 2);   // words 2: the weighted (sampled) variant
     if (method == 1) return fan_kernel(D, (int)words, persistent);
     (void)persistent;   // every run is a persistent launch (a plain run has one job per launch)
+    if (words == 1) return cls_fn(D, block);   // method 0, words 1: the class-sharing variant
     return persistent_fn(D, block);
 }
 

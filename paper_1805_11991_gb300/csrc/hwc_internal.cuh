@@ -189,6 +189,16 @@ struct KJob {
     uint32_t *mweight;
     uint64_t s_first, s_count;
     uint64_t w_first, w_n;            // mweight[i - w_first] for members w_first <= i < w_first + w_n
+    // class-sharing kernel (method 0 with words = 1, classes.cuh): the samples
+    // sorted by class c = (c_2..c_{d-2}) before the count (launch_class_sort);
+    // cls_sorted holds c_0 + c_1 q of each sample, grouped by class;
+    // cls_cnt[c] = end of class c in cls_sorted after the sort;
+    // cls_tiles[t] = (class, start) of up to 32 samples, class 0xFFFFFFFF past
+    // the last tile (n_tiles is the bound ceil(count / 32) + cls_n)
+    uint2 *cls_tiles;
+    uint32_t *cls_cnt;
+    uint32_t *cls_sorted;
+    uint32_t cls_n;                   // classes: q^(d-3)
 };
 
 // launch helpers (count_kernels.cu)
@@ -208,6 +218,8 @@ int launch_compact(const KJob *d_jobs, uint32_t n_jobs, cudaStream_t s);
 // the multiplicities kj.mweight of a sampled job counted by the two-level
 // kernel: cleared, then one atomic add per sample (stream-ordered)
 int launch_sample_weights(const KJob &kj, cudaStream_t s);
+// sort the samples of a class-sharing job by class (no-op for other jobs)
+int launch_class_sort(const KJob &kj, cudaStream_t s);
 // raise the dynamic shared memory limit of the count kernels (once per device)
 int prepare_count_kernels(void);
 int max_ctas_per_sm(int D, uint32_t method, uint32_t words, int block, uint32_t smem_bytes,
@@ -233,6 +245,13 @@ inline bool needs_weights(const KJob &kj)
 // fill_kjob flag (internal): keep sampled families on the per-member kernel
 // (per-sample outputs need the members in sample order)
 constexpr uint32_t kFlagNoWeights = 1u << 31;
+// fill_kjob flag (internal): no class-sharing kernel (the server's requests
+// are slices too small to share chains)
+constexpr uint32_t kFlagNoClass = 1u << 30;
+// the class-sharing kernel needs this many samples per class on average
+constexpr uint64_t kClsMinPerClass = 16;
+constexpr uint32_t kClsWarpBytes = 512;   // class-sharing kernel: per-warp staging of 64 (log u, log x)
+constexpr uint32_t kClsMaxWarps = 24;
 // the points field k (1-based) evaluates: one per Frobenius orbit (orbits,
 // k >= 2) or all of F_Q^x; and the two-level kernel's zero shift
 void set_points(KJob &kj, uint32_t k, const Tables *t, bool orbits);
@@ -253,6 +272,8 @@ const void *horner_kernel(int D, int which);
 const void *horner_kernel_a(int D, int which);   // horner_a.cu, D = 3..6
 const void *horner_kernel_b(int D, int which);   // horner_b.cu, D = 7, 8
 const void *horner_kernel_c(int D, int which);   // horner_c.cu, D = 9, 10
+// class-sharing kernels (classes.cuh), D = 3..6: which = 1 (<= 256 threads) or 3 (<= 768)
+const void *cls_kernel_a(int D, int which);   // cls_a.cu
 // c_0 fan-out kernels (fanout.cuh), W = row words
 const void *fan_kernel(int D, int W, bool persistent);
 const void *fan_kernel_a(int D, int W, bool persistent);   // fanout_a.cu, D = 3, 4

@@ -161,10 +161,12 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit, bool no_triple)
         if (j.method == 2) b += 16 + (uint64_t)kFan2WarpsHost * fan2_warp_bytes(j.q, false);   // smallest block
         return b;
     };
+    // the class-sharing variant of the per-member kernel stages points per warp
+    const uint64_t cls_bytes = (j.method == 0 && j.words == 1) ? 16ull + kClsMaxWarps * kClsWarpBytes : 0ull;
     auto bytes_for = [&](void) {
         uint64_t u16 = 0;
         for (uint32_t k = 0; k < j.g; ++k) u16 += words(k);
-        return u16 * 2 + 4ull * j.g * ((j.q + 3) / 4) * 4 + fan_bytes();
+        return u16 * 2 + 4ull * j.g * ((j.q + 3) / 4) * 4 + fan_bytes() + cls_bytes;
     };
     // int16 rows, largest field first, while that makes room for 16 warps
     if (j.method == 2 && j.g == 4 && j.q <= 15) {
@@ -261,6 +263,12 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit, bool no_triple)
         j.warp_off = bytes;
         j.warp_bytes = fan2_warp_bytes(j.q, j.dense_off != 0);
         bytes += kFan2WarpsHost * j.warp_bytes;
+    }
+    if (cls_bytes) {   // room for the largest block of the per-member kernels
+        bytes = (bytes + 15) / 16 * 16;
+        j.warp_off = bytes;
+        j.warp_bytes = kClsWarpBytes;
+        bytes += kClsMaxWarps * kClsWarpBytes;
     }
     j.smem_bytes = bytes;
     return true;
@@ -542,6 +550,22 @@ int fill_kjob(const hwc_job_t &jb, KJob &kj, uint64_t *fam_n, uint32_t flags, co
         kj.first_group = 0;
         kj.n_tiles = (jb.count + kTileMembers - 1) / kTileMembers;
     }
+    // a sparse sample with many draws per class of high digits (c_2..c_{d-2}):
+    // the class-sharing variant of the per-member kernel (doubled tables)
+    if (kj.method == 0 && jb.family.kind == HWC_FAM_MONIC_NOSUB_SAMPLED && kj.d >= 3 && kj.d <= 6 &&
+        !(flags & (HWC_FLAG_HORNER | HWC_FLAG_LAMBDA | kFlagNoWeights | kFlagNoClass)) &&
+        jb.count < (1ull << 27)) {
+        uint64_t ncls = 1;
+        if (upow(jb.q, kj.d - 3, &ncls) && ncls < (1ull << 31) && jb.count >= kClsMinPerClass * ncls) {
+            kj.words = 1;
+            kj.cls_n = (uint32_t)ncls;
+            kj.n_tiles = (jb.count + 31) / 32 + ncls;
+            if (layout_job_smem(kj, limit, true)) return HWC_OK;
+            kj.words = 0;
+            kj.cls_n = 0;
+            kj.n_tiles = (jb.count + kTileMembers - 1) / kTileMembers;
+        }
+    }
     layout_job_smem(kj, limit, no_triple);
     return HWC_OK;
 }
@@ -738,7 +762,7 @@ static int batch_enqueue(hwc_batch *b, cudaStream_t s, bool capturing)
     int rc = launch_clear(b->d_jobs, nj, b->d_counters, (uint32_t)b->groups.size(), s);
     if (rc) return rc;
     for (const HostJob &hj : b->jobs)   // multiplicities of the samples counted over whole families
-        if ((rc = launch_sample_weights(hj.kj, s))) return rc;
+        if ((rc = launch_sample_weights(hj.kj, s)) || (rc = launch_class_sort(hj.kj, s))) return rc;
     // inside a graph capture an event record must be an external node to time anything
     if (b->t0) HWC_CUDA_TRY(capturing ? cudaEventRecordWithFlags(b->t0, s, cudaEventRecordExternal)
                                       : cudaEventRecord(b->t0, s));
@@ -896,7 +920,9 @@ static int batch_create_impl(const hwc_job_t *jobs, size_t n, uint32_t flags, ui
         if ((rc = dalloc(b, &kj.hkeys, cap)) || (rc = dalloc(b, &kj.hcounts, cap)) ||
             (rc = dalloc(b, &kj.stats, 4)) || (rc = dalloc(b, &kj.out_keys, cap)) ||
             (rc = dalloc(b, &kj.out_counts, cap)) || (rc = dalloc(b, &kj.n_out, 1)) ||
-            (needs_weights(kj) && (rc = dalloc(b, &kj.mweight, kj.w_n)))) {
+            (needs_weights(kj) && (rc = dalloc(b, &kj.mweight, kj.w_n))) ||
+            (kj.cls_n && ((rc = dalloc(b, &kj.cls_cnt, kj.cls_n)) || (rc = dalloc(b, &kj.cls_tiles, kj.n_tiles)) ||
+                          (rc = dalloc(b, &kj.cls_sorted, kj.count))))) {
             batch_release(b);
             return rc;
         }
@@ -1099,7 +1125,8 @@ extern "C" int hwc_batch_job_method(const hwc_batch_t *b, size_t i, uint32_t *me
 {
     if (!b || !method) return set_error(HWC_ERR_ARG, "null argument");
     if (i >= b->pos.size()) return set_error(HWC_ERR_RANGE, "job %zu of %zu", i, b->pos.size());
-    *method = b->jobs[b->pos[i]].kj.method;
+    const KJob &kj = b->jobs[b->pos[i]].kj;
+    *method = (kj.method == 0 && kj.cls_n) ? 3u : kj.method;   // 3: the class-sharing variant
     return HWC_OK;
 }
 

@@ -464,7 +464,7 @@ extern "C" int hwc_serve_submit(hwc_server_t *s, const hwc_job_t *job, uint64_t 
     uint64_t fam_n = 0;
     TuneChoice tc;   // a choice the autotuner already made for this class (no measuring here)
     tune_lookup(*job, 0, &tc);
-    int rc = fill_kjob(*job, r->kj, &fam_n, 0, &tc);   // validates, builds tables
+    int rc = fill_kjob(*job, r->kj, &fam_n, kFlagNoClass, &tc);   // validates, builds tables
     if (rc) {
         delete r;
         return rc;
