@@ -119,6 +119,13 @@ def config3_q293_slice():
     return [JobSpec(2, 293, MONIC_NOSUB_SAMPLED, 5, 0, 1 << 18, seed=7, sample_count=1 << 24)]
 
 
+def config3_q293_cls_slice():
+    """The first 2^21 of the 2^24 sampled members of the q=293 job of
+    configuration 3 (about 24 samples per class of (c_2, c_3)): the small case
+    used for profiles of the class-sharing kernel."""
+    return [JobSpec(2, 293, MONIC_NOSUB_SAMPLED, 5, 0, 1 << 21, seed=7, sample_count=1 << 24)]
+
+
 def config5_q13_slice():
     """2^20 members from the middle of the full g=4 q=13 degree-9 family (6,205
     groups of q^2 members): the small case used for profiles of the two-level
@@ -130,7 +137,7 @@ def config5_q13_slice():
 CONFIGS = {"config1": config1, "config2": config2, "config3": config3, "config4": config4,
            "config5": config5, "config2_q31d5": config2_q31d5, "config2_q31d6": config2_q31d6,
            "config4_q27_slice": config4_q27_slice, "config3_q293_slice": config3_q293_slice,
-           "config5_q13_slice": config5_q13_slice}
+           "config5_q13_slice": config5_q13_slice, "config3_q293_cls_slice": config3_q293_cls_slice}
 
 
 def poisson_arrivals(n: int, rate_per_s: float, seed: int = 11) -> np.ndarray:
