@@ -349,7 +349,7 @@ __device__ __forceinline__ void group2_field(const KJob &J, int k, const uint8_t
                 else fan2_block<false, QUEUE>(T, rows, Us + i0 + t0, L, lb, b0, 0u, rq, qn, a);
                 if (!REPS) lb = addmod(lb, 8u % L, L);
                 const uint32_t e = csa8(P, a);
-                if (QUEUE && __any_sync(0xFFFFFFFFu, qn >= 32 * (kFan2Queue - 8 + 1))) {   // more than 8 entries
+                if (QUEUE && __any_sync(0xFFFFFFFFu, qn >= 32 * (kFan2Queue - 8 + 1))) {   // room for fewer than 8 more
                     drain_queue(rq, qn, lane, zdig, zdiv, L, acc_row, zw);
                     qn = (uint32_t)lane;
                 }
@@ -384,7 +384,7 @@ __device__ __forceinline__ void group2_field(const KJob &J, int k, const uint8_t
                     flush_planes(P, acc_row, J.q, true);
                     nblk = 0;
                 }
-                if (QUEUE && __any_sync(0xFFFFFFFFu, qn >= 32 * (kFan2Queue - 8 + 1))) {   // more than 8 entries
+                if (QUEUE && __any_sync(0xFFFFFFFFu, qn >= 32 * (kFan2Queue - 8 + 1))) {   // room for fewer than 8 more
                     drain_queue(rq, qn, lane, zdig, zdiv, L, acc_row, zw);
                     qn = (uint32_t)lane;
                 }
@@ -406,7 +406,7 @@ __device__ __forceinline__ void group2_field(const KJob &J, int k, const uint8_t
                     flush_planes(P, acc_row, J.q, true);
                     nblk = 0;
                 }
-                if (QUEUE && __any_sync(0xFFFFFFFFu, qn >= 32 * (kFan2Queue - 8 + 1))) {   // more than 8 entries
+                if (QUEUE && __any_sync(0xFFFFFFFFu, qn >= 32 * (kFan2Queue - 8 + 1))) {   // room for fewer than 8 more
                     drain_queue(rq, qn, lane, zdig, zdiv, L, acc_row, zw);
                     qn = (uint32_t)lane;
                 }

@@ -295,11 +295,11 @@ constexpr int kFan2WarpsHost = 4;   // warps per CTA of the two-level kernel
 //   Dd[us] u32: staged log u(x) - log x (orbit points)
 //   acc[32][q] u16: per-lane rows of 2 cnt + z for every c_0 (lane s q + b
 //              holds (c_1 = b, chunk s); lanes past S q fill unused rows)
-//   rq[16][32] u16: per-lane queue of row indices with a zero digit
+//   rq[kFan2Queue][32] u16: per-lane queue of row indices with a zero digit
 //   sqf[ceil(q^2/32)] u32: square-free member bits
 //   par[64] u32: the group's digits c_i, the field's logs lam_i and h chain
 //   a1[q^2] u16 (dense histogram only): a_1 + 32768 of every member
-constexpr uint32_t kFan2Queue = 16;
+constexpr uint32_t kFan2Queue = 14;   // drained once a lane holds more than 6 (a block adds up to 8)
 // The two-level kernel stages each Zech table behind a prefix of 64 entries
 // (the table continued periodically to negative indices) with the poison
 // value 0xFFFF, and each fan-out row table as rows[i mod L] for i < L + 8

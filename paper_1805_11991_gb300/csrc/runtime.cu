@@ -179,6 +179,13 @@ bool layout_job_smem(KJob &j, uint32_t smem_limit, bool no_triple)
             r16[big] = 1;
             kind[big] = kTabDoubleSmem;
         }
+        // still short of 16 warps: int16-row fields give up the pad word when
+        // the lanes' Zech reads (log b apart, word stride s / 2) already fall
+        // on distinct banks (s / 2 not a multiple of 4)
+        for (uint32_t k = 0; k < j.g && bytes_for() + extra > smem_limit; ++k) {
+            const uint32_t s = j.L[k] / (j.q - 1);
+            if (r16[k] && pad[k] && (s / 2) % 4 != 0) pad[k] = 0;
+        }
     }
     // the two-level kernel reads its Zech tables only in the shared chain: give
     // up tripled tables, largest first, while that makes room for 16 warps
