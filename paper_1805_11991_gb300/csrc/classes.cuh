@@ -32,12 +32,13 @@ __device__ __forceinline__ void cls_points(const Tab T, uint32_t L, const uint2 
                                            uint32_t l0, bool z1, bool z0, int &odd, int &zeros)
 {
     const uint32_t cap = 2 * L;
+#pragma unroll 4
     for (uint32_t p = 0; p < nb; ++p) {
         const uint2 ux = st[p];
         const uint32_t U = ux.x, X = ux.y;
         uint32_t lcx = l1 + X;
         lcx = min(lcx, lcx - L);                       // log(c_1 x) in [0, L)
-        const uint32_t i1 = min(U + L - lcx, cap);     // u = 0 (U = L) reads the poison at 2L
+        const uint32_t i1 = U + L - lcx;               // in (0, 2L]: u = 0 (U = L) and lcx = 0 read the poison at 2L
         const uint32_t t1 = lcx + T[i1];
         uint32_t ly = min(t1, t1 - L);                 // log y; >= L when y = 0 or u = 0
         ly = z1 ? U : ly;                              // c_1 = 0: y = u
