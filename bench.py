@@ -20,6 +20,9 @@ At one GPU the line also carries, each with its own device times:
   config2 = g=2, q = 31 and 27, batched;
   served  = configuration 2 as Poisson-timed requests through the server
             (p50/p99 latency, results against the batched histograms);
+  config5, served_config5 = the genus-4 served workload (q = 7, 9, 11 and
+            2^26 draws over F_13), batched, then as requests (the draws cut
+            into windows of members);
   table1  = the paper's Table 1 workload: one curve over F_{p^2}, p = 101..3001
             (hwc_curve_count), beside the paper's times.
 Under torchrun (N > 1) every job's member range is split across the ranks
@@ -59,7 +62,7 @@ def parse():
     ap.add_argument("--impl", default="hwc", choices=["hwc", "reference"])
     ap.add_argument("--config", default="config4", choices=sorted(CONFIGS))
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the config3 / config2 / served extras of the one-GPU line")
+                    help="skip the config3 / config2 / served / config5 / table1 extras of the one-GPU line")
     ap.add_argument("--extra-steps", type=int, default=2,
                     help="timed steps of the config3 extra (batched and plain each)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -626,6 +629,13 @@ def main():
         line["served"] = serve_leg(hwc, c2_jobs, c2_results, c2["batched"]["value"], args.serve_requests,
                                    args.serve_load)
         line["served"]["workload"] = "config2"
+        if args.config != "config5":   # the genus-4 served workload: batched, then as requests
+            c5, c5_jobs, c5_results = extra_workload(hwc, "config5", args.extra_steps, ew, stream, flush,
+                                                     plain=False)
+            line["config5"] = c5
+            line["served_config5"] = serve_leg(hwc, c5_jobs, c5_results, c5["batched"]["value"],
+                                               args.serve_requests, args.serve_load)
+            line["served_config5"]["workload"] = "config5"
         line["table1"] = table1_leg(hwc)
     if args.serve and rank == 0 and world == 1:
         line["served_" + args.config] = serve_leg(hwc, jobs, results, value, args.serve_requests, args.serve_load)
