@@ -47,7 +47,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_1805_11991_gb300.workloads import CONFIGS, MONIC_NOSUB_SAMPLED, JobSpec  # noqa: E402
+from paper_1805_11991_gb300.workloads import CONFIGS, MONIC_NOSUB_SAMPLED, JobSpec, shard_job  # noqa: E402
 
 METRIC = "point evals/s (square-free members x sum_k q^k), batched persistent launch"
 UNIT = "evals/s"
@@ -500,11 +500,9 @@ def main():
     from paper_1805_11991_gb300 import hwc, shard
 
     full_jobs = CONFIGS[args.config]()
-    # each rank takes a contiguous shard of every job's member range
-    jobs = []
-    for s in full_jobs:
-        a, n = shard.shard_range(s.first, s.n(), rank, world)
-        jobs.append(s.with_range(a, n))
+    # each rank takes a contiguous shard of every job's member range (a
+    # densely drawn sample: a window of its family with the draws in it)
+    jobs = full_jobs if world == 1 else [shard_job(s, rank, world) for s in full_jobs]
     hjobs = _hjobs(hwc, jobs)
     tune = hwc.FLAG_NO_TUNE if args.no_tune else 0
     batched = hwc.Batch(hjobs, flags=hwc.FLAG_GRAPH | hwc.FLAG_TIMING | tune)

@@ -146,21 +146,45 @@ def poisson_arrivals(n: int, rate_per_s: float, seed: int = 11) -> np.ndarray:
     return np.cumsum(rng.exponential(1.0 / rate_per_s, size=n))
 
 
-def split_job(job: JobSpec, parts: int):
-    """Cut a job's member range into `parts` contiguous slices (serving requests,
-    shards)."""
-    n = job.n()
-    out = []
-    if job.whole_family_draws() and job.first == 0 and n == job.sample_count:
-        # a densely drawn sample: windows of the enumerated family, each with
-        # the draws that land in it (their union is the whole sample)
+def _cut_by_windows(job: JobSpec) -> bool:
+    """A whole densely drawn sample: cut it into windows of the enumerated
+    family, each with the draws that land in it (their union is the whole
+    sample), not into slices of the draws, which would each be too sparse
+    for the whole-family kernel."""
+    return job.whole_family_draws() and job.first == 0 and job.n() == job.sample_count
+
+
+def _part(job: JobSpec, i: int, parts: int) -> JobSpec:
+    """Part i of `parts` of a job: a contiguous slice of its range, or a
+    window of its family (see _cut_by_windows)."""
+    if _cut_by_windows(job):
         fam = job.q ** (job.degree - 1)
+        a, b = (fam * i) // parts, (fam * (i + 1)) // parts
+        return JobSpec(job.g, job.q, MONIC_NOSUB_SAMPLED_WINDOW, job.degree, a, b - a, job.seed, job.sample_count)
+    n = job.n()
+    a = job.first + (n * i) // parts
+    b = job.first + (n * (i + 1)) // parts
+    return job.with_range(a, b - a)
+
+
+def shard_job(job: JobSpec, rank: int, world: int) -> JobSpec:
+    """This rank's share of a job when every rank counts one part on its own
+    GPU (possibly empty)."""
+    return _part(job, rank, world)
+
+
+def split_job(job: JobSpec, parts: int):
+    """Cut a job into `parts` pieces of about equal work (serving requests):
+    contiguous slices of its member range, or windows of a densely drawn
+    sample's family; empty pieces are left out."""
+    out = []
+    if _cut_by_windows(job):
         for i in range(parts):
-            a, b = (fam * i) // parts, (fam * (i + 1)) // parts
-            if b > a:
-                out.append(JobSpec(job.g, job.q, MONIC_NOSUB_SAMPLED_WINDOW, job.degree, a, b - a, job.seed,
-                                   job.sample_count))
+            w = _part(job, i, parts)
+            if w.n() > 0:
+                out.append(w)
         return out
+    n = job.n()
     for i in range(parts):
         a = job.first + (n * i) // parts
         b = job.first + (n * (i + 1)) // parts
