@@ -725,7 +725,7 @@ __device__ __forceinline__ void process_group2(const KJob &J, uint64_t gtile, co
     __syncwarp();
     if ((uint32_t)lane < q) {
         uint32_t mask;
-        if constexpr (D <= 8) {   // f' of full degree: the fixed-shape form
+        if constexpr (D <= 10) {   // f' of full degree: the fixed-shape form
             if (mulT[(D % J.p) * q + gc[D]] != 0) mask = sqf_mask_full<D>(mulT, subT, invT, addT, q, J.p, gc, (uint32_t)lane);
             else mask = sqf_mask_for_b<D>(mulT, subT, invT, addT, q, J.p, gc, (uint32_t)lane);
         } else {
