@@ -365,6 +365,9 @@ int hwc_curve_count(uint32_t q, uint32_t k, uint32_t d, uint64_t n, const uint32
  *    32768 hash slots (min(count, Hasse-Weil box, number of real Weil
  *    polynomials of degree g for q) above 16384) are rejected
  *    with HWC_ERR_TOO_LARGE before anything runs.
+ *  - Families: HWC_FAM_ALL_DEG, HWC_FAM_MONIC_NOSUB and
+ *    HWC_FAM_MONIC_NOSUB_SAMPLED (each sample counted for itself); the
+ *    reduced and windowed families give HWC_ERR_ARG.
  *  - tables[k-1] (k = 1..g) are handles from hwc_field_tables(q, k), built
  *    beforehand; they are read, not changed.
  *  - Outputs are DEVICE buffers owned by the caller: counts[max_entries*g]

@@ -431,7 +431,8 @@ extern "C" int hwc_count_noalloc(uint32_t g, uint32_t q, const hwc_family_t *fam
     if (g < 1 || g > (uint32_t)kMaxG) return set_error(HWC_ERR_ARG, "g=%u outside [1,%d]", g, kMaxG);
     const uint32_t d = fam->degree;
     if (d != 2 * g + 1 && d != 2 * g + 2) return set_error(HWC_ERR_ARG, "degree %u is not 2g+1 or 2g+2", d);
-    if (fam->kind > HWC_FAM_MONIC_NOSUB_SAMPLED) return set_error(HWC_ERR_ARG, "unknown family kind");
+    if (fam->kind > HWC_FAM_MONIC_NOSUB_SAMPLED)
+        return set_error(HWC_ERR_ARG, "family kind %u is not counted without allocation", fam->kind);
     uint64_t fam_n = 0;
     int rc = hwc_family_size(q, fam, &fam_n);
     if (rc) return rc;
